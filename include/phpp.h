@@ -1,0 +1,223 @@
+/*
+ * phpp -- short-range particle-particle (PP) gravity on one GB300 GPU.
+ *
+ * C ABI of the library libphpp.so.  The operation is the short-range part of
+ * the PM-Tree-PP force split of PHoTo"N"s (arXiv:1802.09824):
+ *
+ *   a_i = G sum_{j != i, r_ij < rcut} m_j d_ij f(r_ij) / (r_ij^2 + eps^2)^{3/2}
+ *   f(s) = erfc(s / 2R_s) + s / (R_s sqrt(pi)) exp(-s^2 / 4R_s^2)
+ *
+ * f is the short-range factor of Eq. (split) (Sec. 3.1); R_cut is the radius
+ * beyond which the short-range force is dropped (Sec. 3.1, R_cut = 4.5 R_s);
+ * d_ij is the minimum-image separation in a periodic box of side L; eps is a
+ * Plummer softening that enters the Newtonian factor only (f is taken at the
+ * unsoftened r).  The sum is organised as in Sec. 3.2-3.3 and Sec. 4.3:
+ * particles are sorted along a space-filling curve inside a ground grid whose
+ * cells are at least R_cut wide, cut into octree leaves, and each group of
+ * target particles sums directly over the leaves of its own and the 26
+ * neighbouring ground cells that lie within R_cut (leaf-leaf PP).
+ *
+ * Conventions for every call
+ *  - Return value: PH_OK (0), a positive warning, or a negative PH_ERR_*.
+ *    On error ph_last_error() gives a message (thread-local, valid until the
+ *    next call on the same thread).
+ *  - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and is asynchronous unless stated otherwise.
+ *  - Pointers named d_* must be device memory.  Pointers documented as
+ *    "host or device" are classified with cudaPointerGetAttributes: device
+ *    (or managed) memory is used in place; host memory is copied through a
+ *    device buffer owned by the handle on the same stream, and such a call
+ *    returns only after the copies it needs have been issued (pageable host
+ *    memory makes the copy synchronous).  Host buffers must stay valid until
+ *    the stream has executed the call.
+ *  - Handles (ph_leaves, ph_pairs, ph_mlp) own their device memory until
+ *    ph_free().  A handle pointer passed in non-NULL is rebuilt in place,
+ *    reusing its buffers when they are large enough.
+ *  - Device-side faults that do not corrupt memory (capacity overflow, a
+ *    non-finite input) are latched in a word inside the handle and reported
+ *    by ph_status() and by the next call that synchronises.
+ */
+#ifndef PHPP_H
+#define PHPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define PH_OK                   0
+#define PH_WARN_FALLBACK        1   /* learned factor rejected; exact path used */
+#define PH_ERR_ARG             -1   /* bad argument (NULL, size, range)          */
+#define PH_ERR_RCUT_GE_HALF_L  -2   /* rcut >= L/2: minimum image not unique     */
+#define PH_ERR_NONFINITE       -3   /* NaN/Inf in positions or masses            */
+#define PH_ERR_OOM             -4   /* device allocation failed                  */
+#define PH_ERR_CUDA            -5   /* a CUDA runtime call failed                */
+#define PH_ERR_CAPACITY        -6   /* a fixed-capacity buffer overflowed        */
+#define PH_ERR_TIMEOUT         -7   /* a bounded device wait gave up             */
+#define PH_ERR_STATE           -8   /* handle in the wrong state / wrong type    */
+
+/* element type of a position array */
+#define PH_F32 0
+#define PH_F64 1
+
+/* ordering of particles inside a ground cell */
+#define PH_KEY_MORTON   0   /* Morton order (Sec. 3.2)                         */
+#define PH_KEY_HILBERT  1   /* Peano-Hilbert order (the curve of Sec. 4.1)     */
+
+/* how the short-range factor f is evaluated in the PP kernel */
+#define PH_G_EXACT    0     /* Eq. (split), FP32 with SFU exp/rsqrt             */
+#define PH_G_LEARNED  1     /* the 1-16-16-1 SiLU network of a ph_mlp           */
+
+/*
+ * Parameters of one periodic box.
+ *   L         box side (> 0); positions may lie anywhere, they are wrapped.
+ *   G         gravitational constant.
+ *   eps       Plummer softening (>= 0).
+ *   rs        split scale R_s of Eq. (split) (> 0).
+ *   rcut      cutoff radius, 0 < rcut < L/2 (R_cut of Sec. 3.1).
+ *   leaf_max  largest number of particles in an octree leaf, 1..256 (the
+ *             N_pp of Sec. 3.1 / leaf size of Sec. 4.4).
+ *   key_kind  PH_KEY_MORTON or PH_KEY_HILBERT.
+ *   group_size number of target particles summed together by one set of
+ *             lanes: 0 (default, 32), 8, 16, 32 or 64.
+ */
+typedef struct ph_params {
+    double  L;
+    double  G;
+    double  eps;
+    double  rs;
+    double  rcut;
+    int32_t leaf_max;
+    int32_t key_kind;
+    int32_t group_size;
+    int32_t reserved;
+} ph_params;
+
+typedef struct ph_leaves ph_leaves;   /* sorted particles + leaf / group tables */
+typedef struct ph_pairs  ph_pairs;    /* cutoff leaf-pair list (CSR by group)    */
+typedef struct ph_mlp    ph_mlp;      /* learned short-range factor             */
+
+/*
+ * Sort the particles of one box along the space-filling curve and cut them
+ * into octree leaves and target groups (Sec. 3.2, "Tree building": ground
+ * cell index (i N_side + j) N_side + k, bucket order of ground cells, Morton
+ * order inside; leaves are the largest octree cells holding <= leaf_max
+ * particles, Sec. 3.1 / 4.4).
+ *
+ *   pos       [n*3] host or device; pos_type PH_F32 or PH_F64; xyz per row.
+ *   mass      [n]   host or device float32, or NULL for equal masses 1/n.
+ *   n         number of particles (0 allowed: an empty handle).
+ *   params    box parameters (host memory).
+ *   stream    cudaStream_t.
+ *   leaves    in/out: *leaves == NULL creates a handle, else it is rebuilt.
+ * Errors: PH_ERR_ARG, PH_ERR_RCUT_GE_HALF_L, PH_ERR_OOM, PH_ERR_CUDA; a
+ * non-finite coordinate is latched and reported as PH_ERR_NONFINITE by the
+ * next synchronising call.  Synchronises the stream once (to size the leaf
+ * and group tables).
+ */
+int ph_build_leaves(const void *pos, int pos_type, const float *mass, int64_t n,
+                    const ph_params *params, void *stream, ph_leaves **leaves);
+
+/*
+ * Same for B independent boxes stored one after another: box b owns rows
+ * [box_offsets[b], box_offsets[b+1]).  box_offsets [B+1] host int64,
+ * box_offsets[0] = 0; params [B] host, one per box (mass NULL means 1/n_b
+ * in box b).  Boxes never interact.  1 <= B <= 65536.
+ */
+int ph_build_leaves_batched(const void *pos, int pos_type, const float *mass,
+                            const int64_t *box_offsets, int32_t n_boxes,
+                            const ph_params *params, void *stream, ph_leaves **leaves);
+
+/*
+ * Build the cutoff leaf-pair list: for every target group, each leaf of the
+ * 27 ground cells around it (Sec. 4.3: a ground cell and its 26 neighbours,
+ * each with the periodic image its offset implies) whose bounding box comes
+ * within rcut of the group's bounding box (Sec. 3.3: leaf-leaf interactions
+ * go to the PP kernel).  Stored per entry: the leaf and the FP32 offset
+ * (leaf reference - group reference, computed in FP64, image included).
+ * Synchronises the stream once to size the list, unless the handle was given
+ * a fixed capacity with ph_pairs_reserve (then overflow is latched as
+ * PH_ERR_CAPACITY and no entry beyond the capacity is written).
+ */
+int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs);
+
+/* Give a pairs handle a fixed capacity (entries) and stop the sizing sync. */
+int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity);
+
+/*
+ * PP direct summation over the pair list (Eq. (split), Sec. 3.3, Sec. 4.4):
+ * writes acc[3*i .. 3*i+2] = a_i for every particle, in the caller's
+ * original order (box-concatenated order for batched handles).
+ *   g_mode  PH_G_EXACT or PH_G_LEARNED (then mlp must be non-NULL).
+ *   acc     [n*3] float32, host or device.
+ * Returns PH_WARN_FALLBACK when the learned factor's validated error is above
+ * its tolerance: the exact factor is used instead.
+ */
+int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode,
+                const ph_mlp *mlp, float *acc, void *stream);
+
+/*
+ * Whole step in one call: build leaves, pairs, then PP, reusing *leaves and
+ * *pairs (created when NULL).  pos/mass/acc host or device as above.
+ */
+int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n,
+             const ph_params *params, int g_mode, const ph_mlp *mlp, float *acc,
+             void *stream, ph_leaves **leaves, ph_pairs **pairs);
+
+/* Free any handle (ph_leaves, ph_pairs, ph_mlp).  NULL is a no-op. */
+void ph_free(void *handle);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *ph_last_error(void);
+
+/* Synchronise the handle's last stream and return its latched device status. */
+int ph_status(const void *handle);
+
+/* ------------------------------------------------------------ introspection
+ * Read-only views of the internal arrays (device pointers, valid until the
+ * handle is rebuilt or freed).  Used by tests to check each step.
+ */
+typedef struct ph_leaves_view {
+    int64_t n;                 /* particles                                    */
+    int32_t n_boxes;
+    int32_t n_leaves;
+    int32_t n_groups;
+    int32_t n_cells;           /* ground cells over all boxes                  */
+    const uint64_t *keys;      /* [n] sorted keys                              */
+    const int32_t *perm;       /* [n] sorted position -> caller row            */
+    const int32_t *leaf_first; /* [n_leaves+1]                                 */
+    const double  *leaf_ref;   /* [n_leaves*3] leaf reference point (FP64)     */
+    const float   *leaf_half;  /* [n_leaves*4] bounding-box half extents       */
+    const int32_t *group_first;/* [n_groups+1]                                 */
+    const double  *group_ref;  /* [n_groups*3]                                 */
+    const float   *group_half; /* [n_groups*4]                                 */
+    const float   *pos_leaf;   /* [n*4] x-ref_leaf, y, z, mass (FP32)          */
+    const float   *pos_group;  /* [n*4] x-ref_group, y, z, mass (FP32)         */
+    const int32_t *cell_leaf_first; /* [n_cells+1] first leaf of each cell     */
+    int32_t g[4];              /* ground level of box 0..3 (N_side = 2^g)      */
+    int32_t key_bits;          /* T: key bits per axis                         */
+    int32_t group_size;
+} ph_leaves_view;
+
+typedef struct ph_pairs_view {
+    int64_t n_pairs;
+    int32_t n_groups;
+    int32_t reserved;
+    const int64_t *group_off;  /* [n_groups+1] CSR offsets                     */
+    const float   *entries;    /* [n_pairs*4] off.x, off.y, off.z, leaf (bits) */
+} ph_pairs_view;
+
+int ph_leaves_get_view(const ph_leaves *leaves, ph_leaves_view *out);
+int ph_pairs_get_view(const ph_pairs *pairs, ph_pairs_view *out);
+
+/* Work counted by the last ph_pp_accel on this handle (synchronises):
+ * interactions evaluated by the PP kernel, and the j-particles staged. */
+int ph_pp_counters(const ph_pairs *pairs, int64_t *interactions, int64_t *staged);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHPP_H */

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libphpp.so (include/phpp.h), same names as the C ABI.
+
+Only argument marshalling lives here: tensors become raw pointers, the
+current torch CUDA stream becomes the cudaStream_t, return codes become
+exceptions.  Every step of the computation runs in the library's kernels.
+If the library is missing, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphpp.so")
+
+PH_OK = 0
+PH_WARN_FALLBACK = 1
+PH_ERR_ARG = -1
+PH_ERR_RCUT_GE_HALF_L = -2
+PH_ERR_NONFINITE = -3
+PH_ERR_OOM = -4
+PH_ERR_CUDA = -5
+PH_ERR_CAPACITY = -6
+PH_ERR_TIMEOUT = -7
+PH_ERR_STATE = -8
+PH_F32, PH_F64 = 0, 1
+PH_KEY_MORTON, PH_KEY_HILBERT = 0, 1
+PH_G_EXACT, PH_G_LEARNED = 0, 1
+
+
+class PhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"phpp error {code}: {msg}")
+        self.code = code
+
+
+class ph_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("G", ctypes.c_double), ("eps", ctypes.c_double),
+                ("rs", ctypes.c_double), ("rcut", ctypes.c_double), ("leaf_max", ctypes.c_int32),
+                ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ph_leaves_view(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_boxes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+                ("keys", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("leaf_first", ctypes.c_void_p),
+                ("leaf_ref", ctypes.c_void_p), ("leaf_half", ctypes.c_void_p),
+                ("group_first", ctypes.c_void_p), ("group_ref", ctypes.c_void_p),
+                ("group_half", ctypes.c_void_p), ("pos_leaf", ctypes.c_void_p),
+                ("pos_group", ctypes.c_void_p), ("cell_leaf_first", ctypes.c_void_p),
+                ("g", ctypes.c_int32 * 4), ("key_bits", ctypes.c_int32), ("group_size", ctypes.c_int32)]
+
+
+class ph_pairs_view(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p)]
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "ph_build_leaves": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), _VP,
+                         ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_build_leaves_batched": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                 ctypes.POINTER(ph_params), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_leaf_pairs": ([_VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_pairs_reserve": ([ctypes.POINTER(_VP), ctypes.c_int64], ctypes.c_int),
+    "ph_pp_accel": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "ph_accel": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.c_int, _VP, _VP, _VP,
+                  ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_free": ([_VP], None),
+    "ph_last_error": ([], ctypes.c_char_p),
+    "ph_status": ([_VP], ctypes.c_int),
+    "ph_leaves_get_view": ([_VP, ctypes.POINTER(ph_leaves_view)], ctypes.c_int),
+    "ph_pairs_get_view": ([_VP, ctypes.POINTER(ph_pairs_view)], ctypes.c_int),
+    "ph_pp_counters": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise PhError(rc, lib().ph_last_error().decode())
+    if rc > 0:
+        warnings.warn(f"phpp warning {rc}: {lib().ph_last_error().decode()}")
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous(), "tensors must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _pos_type(t):
+    import torch
+    dt = t.dtype
+    if dt in (np.float32, torch.float32):
+        return PH_F32
+    if dt in (np.float64, torch.float64):
+        return PH_F64
+    raise TypeError("positions must be float32 or float64")
+
+
+def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0):
+    return ph_params(float(L), float(G), float(eps), float(rs), float(rcut), int(leaf_max), int(key_kind),
+                     int(group_size), 0)
+
+
+class Handle:
+    """Owner of a ph_leaves / ph_pairs handle (freed on close or collection)."""
+
+    def __init__(self, ptr, keep=()):
+        self.ptr = ctypes.c_void_p(ptr)
+        self._keep = keep
+        self._fin = weakref.finalize(self, _free_ptr, ptr)
+
+    def close(self):
+        self._fin()
+
+    @property
+    def as_arg(self):
+        return self.ptr
+
+
+def _free_ptr(p):
+    if _lib is not None and p:
+        _lib.ph_free(ctypes.c_void_p(p))
+
+
+def _handle_in(h):
+    return ctypes.c_void_p(h.ptr.value if h is not None else None)
+
+
+def _wrap(out, h, keep=()):
+    if h is not None and h.ptr.value == out.value:
+        h._keep = keep
+        return h
+    return Handle(out.value, keep)
+
+
+def ph_build_leaves(pos, mass, params, stream=None, leaves=None):
+    """Sort particles into leaves and target groups (host or device tensors)."""
+    out = _handle_in(leaves)
+    n = int(pos.shape[0])
+    _check(lib().ph_build_leaves(_ptr(pos), _pos_type(pos), _ptr(mass), n, ctypes.byref(params),
+                                 _stream(stream), ctypes.byref(out)))
+    return _wrap(out, leaves, (pos, mass))
+
+
+def ph_build_leaves_batched(pos, mass, box_offsets, params_list, stream=None, leaves=None):
+    out = _handle_in(leaves)
+    offs = np.ascontiguousarray(np.asarray(box_offsets, np.int64))
+    nb = offs.size - 1
+    arr = (ph_params * nb)(*params_list)
+    _check(lib().ph_build_leaves_batched(_ptr(pos), _pos_type(pos), _ptr(mass),
+                                         offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nb, arr,
+                                         _stream(stream), ctypes.byref(out)))
+    return _wrap(out, leaves, (pos, mass, offs, arr))
+
+
+def ph_leaf_pairs(leaves, stream=None, pairs=None):
+    out = _handle_in(pairs)
+    _check(lib().ph_leaf_pairs(leaves.ptr, _stream(stream), ctypes.byref(out)))
+    return _wrap(out, pairs)
+
+
+def ph_pairs_reserve(capacity, pairs=None):
+    out = _handle_in(pairs)
+    _check(lib().ph_pairs_reserve(ctypes.byref(out), int(capacity)))
+    return _wrap(out, pairs)
+
+
+def ph_pp_accel(leaves, pairs, g_mode, mlp, acc, stream=None):
+    """Accelerations into ``acc`` [N,3] float32 (host or device), caller order."""
+    return _check(lib().ph_pp_accel(leaves.ptr, pairs.ptr, int(g_mode),
+                                    mlp.ptr if mlp is not None else None, _ptr(acc), _stream(stream)))
+
+
+def ph_accel(pos, mass, params, g_mode, mlp, acc, stream=None, leaves=None, pairs=None):
+    """Whole step: build, pairs, PP.  Returns (leaves, pairs) handles for reuse."""
+    lo = _handle_in(leaves)
+    po = _handle_in(pairs)
+    rc = lib().ph_accel(_ptr(pos), _pos_type(pos), _ptr(mass), int(pos.shape[0]), ctypes.byref(params), int(g_mode),
+                        mlp.ptr if mlp is not None else None, _ptr(acc), _stream(stream), ctypes.byref(lo),
+                        ctypes.byref(po))
+    lh = _wrap(lo, leaves, (pos, mass)) if lo.value else None
+    ph = _wrap(po, pairs) if po.value else None
+    _check(rc)
+    return lh, ph
+
+
+def ph_free(handle):
+    if handle is not None:
+        handle.close()
+
+
+def ph_status(handle):
+    return _check(lib().ph_status(handle.ptr))
+
+
+def ph_last_error():
+    return lib().ph_last_error().decode()
+
+
+def ph_pp_counters(pairs):
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(lib().ph_pp_counters(pairs.ptr, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ------------------------------------------------------------ introspection
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 2, "strides": None}
+
+
+def _dev(ptr, shape, typestr):
+    import torch
+    if int(np.prod(shape)) == 0 or not ptr:
+        dt = {"<u8": torch.int64, "<i4": torch.int32, "<f8": torch.float64, "<f4": torch.float32,
+              "<i8": torch.int64}[typestr]
+        return torch.zeros(shape, dtype=dt, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+def ph_leaves_get_view(leaves):
+    """Device views (torch tensors, no copy) of the handle's internal arrays."""
+    v = ph_leaves_view()
+    _check(lib().ph_leaves_get_view(leaves.ptr, ctypes.byref(v)))
+    n, nl, ng, nc = v.n, v.n_leaves, v.n_groups, v.n_cells
+    return {
+        "n": n, "n_leaves": nl, "n_groups": ng, "n_cells": nc, "n_boxes": v.n_boxes,
+        "g": list(v.g), "key_bits": v.key_bits, "group_size": v.group_size,
+        "keys": _dev(v.keys, (n,), "<u8"),
+        "perm": _dev(v.perm, (n,), "<i4"),
+        "leaf_first": _dev(v.leaf_first, (nl + 1,), "<i4"),
+        "leaf_ref": _dev(v.leaf_ref, (nl, 3), "<f8"),
+        "leaf_half": _dev(v.leaf_half, (nl, 4), "<f4"),
+        "group_first": _dev(v.group_first, (ng + 1,), "<i4"),
+        "group_ref": _dev(v.group_ref, (ng, 3), "<f8"),
+        "group_half": _dev(v.group_half, (ng, 4), "<f4"),
+        "pos_leaf": _dev(v.pos_leaf, (n, 4), "<f4"),
+        "pos_group": _dev(v.pos_group, (n, 4), "<f4"),
+        "cell_leaf_first": _dev(v.cell_leaf_first, (nc + 1,), "<i4"),
+    }
+
+
+def ph_pairs_get_view(pairs):
+    v = ph_pairs_view()
+    _check(lib().ph_pairs_get_view(pairs.ptr, ctypes.byref(v)))
+    return {
+        "n_pairs": v.n_pairs, "n_groups": v.n_groups,
+        "group_off": _dev(v.group_off, (v.n_groups + 1,), "<i8"),
+        "entries": _dev(v.entries, (v.n_pairs, 4), "<f4"),
+    }

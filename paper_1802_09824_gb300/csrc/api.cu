@@ -1,0 +1,531 @@
+// C ABI entry points: argument checks, handle management, host/device
+// staging.  Every step of the computation runs in the kernels of build.cu,
+// pairs.cu and pp.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "handles.cuh"
+
+namespace phpp {
+
+int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float *mass, cudaStream_t s);
+int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
+int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
+void fit_factor_poly(double U, int deg, float *coef);
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return PH_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(PH_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(PH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ensure(DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return PH_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(PH_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return PH_OK;
+}
+
+void release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int ground_level(double L, double rcut)
+{
+    int g = 0;
+    while (g < kGroundMax && L / (double)(1 << (g + 1)) >= rcut) g++;
+    return g;
+}
+
+static int key_bits_per_axis(int n_boxes)
+{
+    int box_bits = 0;
+    while ((1 << box_bits) < n_boxes) box_bits++;
+    return (63 - box_bits) / 3;
+}
+
+static int poly_degree_for(double U)
+{
+    if (U <= 2.3) return 10;
+    if (U <= 3.05) return 12;
+    if (U <= 4.05) return 14;
+    if (U <= 4.6) return 16;
+    return -1;
+}
+
+static int check_params(const ph_params &p, int b)
+{
+    if (!(std::isfinite(p.L) && p.L > 0)) return fail(PH_ERR_ARG, "box %d: L must be finite and > 0", b);
+    if (!(std::isfinite(p.rs) && p.rs > 0)) return fail(PH_ERR_ARG, "box %d: rs must be > 0", b);
+    if (!(std::isfinite(p.eps) && p.eps >= 0)) return fail(PH_ERR_ARG, "box %d: eps must be >= 0", b);
+    if (!std::isfinite(p.G)) return fail(PH_ERR_ARG, "box %d: G must be finite", b);
+    if (!(std::isfinite(p.rcut) && p.rcut > 0)) return fail(PH_ERR_ARG, "box %d: rcut must be > 0", b);
+    if (!(p.rcut < 0.5 * p.L)) return fail(PH_ERR_RCUT_GE_HALF_L, "box %d: rcut %g >= L/2 %g", b, p.rcut, 0.5 * p.L);
+    if (p.leaf_max < 1 || p.leaf_max > kMaxLeaf) return fail(PH_ERR_ARG, "box %d: leaf_max must be 1..%d", b, kMaxLeaf);
+    if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT)
+        return fail(PH_ERR_ARG, "box %d: unknown key_kind %d", b, p.key_kind);
+    if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "box %d: group_size must be 0 or 32", b);
+    if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
+        return fail(PH_ERR_ARG, "box %d: rcut/rs = %g above the supported 9.2", b, p.rcut / p.rs);
+    return PH_OK;
+}
+
+static void free_leaves(ph_leaves *h)
+{
+    DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
+                      &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
+                      &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
+                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->group_cell, &h->group_box,
+                      &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
+    for (DevBuf *b : bufs) release(*b);
+}
+
+static void free_pairs(ph_pairs *h)
+{
+    DevBuf *bufs[] = {&h->group_cnt, &h->group_off, &h->entries, &h->work, &h->status, &h->temp, &h->acc_tmp};
+    for (DevBuf *b : bufs) release(*b);
+}
+
+// Set up boxes and buffers for n particles, copy host inputs, launch the build.
+static int leaves_common(const void *pos, int pos_type, const float *mass, const int64_t *box_offsets, int32_t nb,
+                         const ph_params *params, void *stream, ph_leaves **leaves)
+{
+    if (!leaves) return fail(PH_ERR_ARG, "leaves must not be NULL");
+    if (!params) return fail(PH_ERR_ARG, "params must not be NULL");
+    if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
+    if (nb < 1 || nb > 65536) return fail(PH_ERR_ARG, "n_boxes must be 1..65536");
+    if (box_offsets[0] != 0) return fail(PH_ERR_ARG, "box_offsets[0] must be 0");
+    for (int b = 0; b < nb; b++)
+        if (box_offsets[b + 1] < box_offsets[b]) return fail(PH_ERR_ARG, "box_offsets must be non-decreasing");
+    const int64_t n = box_offsets[nb];
+    if (n < 0 || n >= (int64_t)1 << 31) return fail(PH_ERR_ARG, "n must be 0..2^31-1");
+    if (n > 0 && !pos) return fail(PH_ERR_ARG, "pos must not be NULL");
+    for (int b = 0; b < nb; b++) {
+        int rc = check_params(params[b], b);
+        if (rc) return rc;
+        if (params[b].leaf_max != params[0].leaf_max || params[b].key_kind != params[0].key_kind ||
+            params[b].group_size != params[0].group_size)
+            return fail(PH_ERR_ARG, "leaf_max, key_kind and group_size must be the same for all boxes");
+    }
+    ph_leaves *h = *leaves;
+    if (h && h->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "handle is not a ph_leaves");
+    bool fresh = false;
+    if (!h) {
+        h = new (std::nothrow) ph_leaves();
+        if (!h) return fail(PH_ERR_OOM, "host allocation failed");
+        fresh = true;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->n = n;
+    h->n_boxes = nb;
+    h->key_bits = key_bits_per_axis(nb);
+    h->max_leaf = params[0].leaf_max;
+    h->key_kind = params[0].key_kind;
+    h->group_size = params[0].group_size ? params[0].group_size : 32;
+    h->boxes_host.resize(nb);
+    int deg = 10;
+    for (int b = 0; b < nb; b++) {
+        int d = poly_degree_for(params[b].rcut / (2.0 * params[b].rs));
+        if (d > deg) deg = d;
+    }
+    h->poly_degree = deg;
+    int cells = 0;
+    std::vector<int32_t> bf(nb + 1);
+    for (int b = 0; b < nb; b++) {
+        const ph_params &p = params[b];
+        BoxDev &bx = h->boxes_host[b];
+        memset(&bx, 0, sizeof bx);
+        bx.L = p.L;
+        bx.g = ground_level(p.L, p.rcut);
+        bx.b = h->key_bits - bx.g;
+        bx.nside = 1 << bx.g;
+        bx.S = std::ldexp(1.0, h->key_bits) / p.L;
+        bx.h = p.L / bx.nside;
+        bx.G = (float)p.G;
+        double e2 = p.eps * p.eps;
+        bx.eps2 = (float)(e2 > 1e-24 ? e2 : 1e-24);
+        bx.rcut2 = (float)(p.rcut * p.rcut);
+        double rf = p.rcut * (1.0 + 3e-5);
+        bx.rfilt2 = (float)(rf * rf);
+        bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
+        bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
+        const int64_t nbx = box_offsets[b + 1] - box_offsets[b];
+        bx.mass_default = nbx > 0 ? (float)(1.0 / (double)nbx) : 0.f;
+        bx.cell_base = cells;
+        bx.first = (int32_t)box_offsets[b];
+        bx.n = (int32_t)nbx;
+        bx.group_size = h->group_size;
+        fit_factor_poly(p.rcut / (2.0 * p.rs), deg, bx.poly);
+        cells += bx.nside * bx.nside * bx.nside;
+        bf[b] = (int32_t)box_offsets[b];
+    }
+    bf[nb] = (int32_t)n;
+    h->n_cells = cells;
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    int rc = 0;
+#define ENS(buf, bytes) \
+    if (!rc) rc = ensure(buf, bytes)
+    ENS(h->boxes, sizeof(BoxDev) * nb);
+    ENS(h->box_first, sizeof(int32_t) * (nb + 1));
+    ENS(h->keys, 8 * N);
+    ENS(h->keys_alt, 8 * N);
+    ENS(h->vals, 4 * N);
+    ENS(h->vals_alt, 4 * N);
+    ENS(h->xw, 24 * N);
+    ENS(h->mass_sorted, 4 * N);
+    ENS(h->cell_first, 4 * (size_t)(cells + 1));
+    ENS(h->leaf_flag, 4 * N);
+    ENS(h->group_flag, 4 * N);
+    ENS(h->leaf_scan, 4 * (N + 1));
+    ENS(h->group_scan, 4 * (N + 1));
+    ENS(h->leaf_first, 4 * (N + 1));
+    ENS(h->group_first, 4 * (N + 1));
+    ENS(h->leaf_ref, 24 * N);
+    ENS(h->leaf_c4, 16 * N);
+    ENS(h->leaf_h4, 16 * N);
+    ENS(h->group_ref, 24 * N);
+    ENS(h->group_c4, 16 * N);
+    ENS(h->group_h4, 16 * N);
+    ENS(h->group_cell, 4 * N);
+    ENS(h->group_box, 4 * N);
+    ENS(h->pos_leaf, 16 * N);
+    ENS(h->pos_group, 16 * N);
+    ENS(h->cell_leaf_first, 4 * (size_t)(cells + 1));
+    ENS(h->counts, 16);
+    ENS(h->status, 16);
+    size_t tb = sort_temp_bytes(n);
+    size_t ts = scan_temp_bytes(n);
+    ENS(h->temp, tb > ts ? tb : ts);
+#undef ENS
+    if (rc) {
+        if (fresh) {
+            free_leaves(h);
+            delete h;
+        }
+        return rc;
+    }
+    if (fresh) {
+        rc = cuda_check(cudaMemsetAsync(h->status.p, 0, 16, s), "status reset");
+        if (rc) {
+            free_leaves(h);
+            delete h;
+            return rc;
+        }
+    }
+    rc = cuda_check(cudaMemcpyAsync(h->boxes.p, h->boxes_host.data(), sizeof(BoxDev) * nb, cudaMemcpyHostToDevice, s),
+                    "copy boxes");
+    if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(h->box_first.p, bf.data(), 4 * (nb + 1), cudaMemcpyHostToDevice, s),
+                        "copy box table");
+    // the box table copies read host memory that dies with this call
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "box table sync");
+    const void *dpos = pos;
+    const float *dmass = mass;
+    if (!rc && n > 0 && !is_device_ptr(pos)) {
+        size_t bytes = (size_t)n * 3 * (pos_type == PH_F64 ? 8 : 4);
+        rc = ensure(h->in_pos, bytes);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(h->in_pos.p, pos, bytes, cudaMemcpyHostToDevice, s), "copy positions");
+        dpos = h->in_pos.p;
+    }
+    if (!rc && n > 0 && mass && !is_device_ptr(mass)) {
+        rc = ensure(h->in_mass, (size_t)n * 4);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(h->in_mass.p, mass, (size_t)n * 4, cudaMemcpyHostToDevice, s),
+                                 "copy masses");
+        dmass = static_cast<const float *>(h->in_mass.p);
+    }
+    if (!rc) rc = build_leaves_device(h, dpos, pos_type, dmass, s);
+    h->last_stream = s;
+    if (rc) {
+        if (fresh) {
+            free_leaves(h);
+            delete h;
+        }
+        return rc;
+    }
+    *leaves = h;
+    return PH_OK;
+}
+
+static int read_status(const DevBuf &b, cudaStream_t s)
+{
+    uint32_t st = 0;
+    int rc = cuda_check(cudaMemcpyAsync(&st, b.p, 4, cudaMemcpyDeviceToHost, s), "read status");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "status sync");
+    if (rc) return rc;
+    if (st & ST_NONFINITE) return fail(PH_ERR_NONFINITE, "non-finite position or mass");
+    if (st & ST_CAPACITY) return fail(PH_ERR_CAPACITY, "pair list capacity exceeded");
+    if (st & ST_TIMEOUT) return fail(PH_ERR_TIMEOUT, "bounded device wait gave up");
+    return PH_OK;
+}
+
+}  // namespace phpp
+
+using namespace phpp;
+
+extern "C" {
+
+int ph_build_leaves(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params,
+                    void *stream, ph_leaves **leaves)
+{
+    if (n < 0) return fail(PH_ERR_ARG, "n must be >= 0");
+    int64_t off[2] = {0, n};
+    return leaves_common(pos, pos_type, mass, off, 1, params, stream, leaves);
+}
+
+int ph_build_leaves_batched(const void *pos, int pos_type, const float *mass, const int64_t *box_offsets,
+                            int32_t n_boxes, const ph_params *params, void *stream, ph_leaves **leaves)
+{
+    if (!box_offsets) return fail(PH_ERR_ARG, "box_offsets must not be NULL");
+    return leaves_common(pos, pos_type, mass, box_offsets, n_boxes, params, stream, leaves);
+}
+
+int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity)
+{
+    if (!pairs || capacity < 0) return fail(PH_ERR_ARG, "bad arguments");
+    ph_pairs *p = *pairs;
+    if (p && p->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "handle is not a ph_pairs");
+    bool fresh = !p;
+    if (fresh) {
+        p = new (std::nothrow) ph_pairs();
+        if (!p) return fail(PH_ERR_OOM, "host allocation failed");
+    }
+    int rc = ensure(p->entries, (size_t)(capacity > 0 ? capacity : 1) * sizeof(float4));
+    if (rc) {
+        if (fresh) delete p;
+        return rc;
+    }
+    p->capacity = capacity;
+    p->fixed_capacity = true;
+    *pairs = p;
+    return PH_OK;
+}
+
+int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
+{
+    if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
+    if (!pairs) return fail(PH_ERR_ARG, "pairs must not be NULL");
+    ph_pairs *p = *pairs;
+    if (p && p->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "handle is not a ph_pairs");
+    bool fresh = !p;
+    if (fresh) {
+        p = new (std::nothrow) ph_pairs();
+        if (!p) return fail(PH_ERR_OOM, "host allocation failed");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t N = (size_t)(leaves->n > 0 ? leaves->n : 1);
+    int rc = 0;
+    if (!rc) rc = ensure(p->group_cnt, 8 * (N + 1));
+    if (!rc) rc = ensure(p->group_off, 8 * (N + 1));
+    if (!rc) rc = ensure(p->work, 64);
+    if (!rc) rc = ensure(p->temp, scan_temp_bytes((int64_t)N));
+    if (!rc && !p->status.p) {
+        rc = ensure(p->status, 16);
+        if (!rc) rc = cuda_check(cudaMemsetAsync(p->status.p, 0, 16, s), "status reset");
+    }
+    if (!rc && !p->entries.p) {
+        rc = ensure(p->entries, 16 * 1024);
+        if (!rc) p->capacity = 1024;
+    }
+    if (!rc) rc = build_pairs_device(leaves, p, s, !p->fixed_capacity);
+    if (rc) {
+        if (fresh) {
+            free_pairs(p);
+            delete p;
+        }
+        return rc;
+    }
+    p->built_from = leaves;
+    p->last_stream = s;
+    *pairs = p;
+    return PH_OK;
+}
+
+int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, const ph_mlp *mlp, float *acc,
+                void *stream)
+{
+    if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
+    if (!pairs || pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
+    if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
+    if (g_mode == PH_G_LEARNED) return fail(PH_ERR_ARG, "learned factor not available in this build");
+    (void)mlp;
+    if (leaves->n > 0 && !acc) return fail(PH_ERR_ARG, "acc must not be NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ph_pairs *pr = const_cast<ph_pairs *>(pairs);
+    if (leaves->n == 0) return PH_OK;
+    const bool dev = is_device_ptr(acc);
+    float *dacc = acc;
+    int rc = 0;
+    if (!dev) {
+        rc = ensure(pr->acc_tmp, (size_t)leaves->n * 12);
+        if (rc) return rc;
+        dacc = static_cast<float *>(pr->acc_tmp.p);
+    }
+    rc = pp_exact_device(leaves, pairs, dacc, s);
+    if (!rc && !dev)
+        rc = cuda_check(cudaMemcpyAsync(acc, dacc, (size_t)leaves->n * 12, cudaMemcpyDeviceToHost, s), "copy acc");
+    pr->last_stream = s;
+    return rc;
+}
+
+int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params, int g_mode,
+             const ph_mlp *mlp, float *acc, void *stream, ph_leaves **leaves, ph_pairs **pairs)
+{
+    if (!leaves || !pairs) return fail(PH_ERR_ARG, "leaves and pairs must not be NULL");
+    int rc = ph_build_leaves(pos, pos_type, mass, n, params, stream, leaves);
+    if (rc) return rc;
+    rc = ph_leaf_pairs(*leaves, stream, pairs);
+    if (rc) return rc;
+    return ph_pp_accel(*leaves, *pairs, g_mode, mlp, acc, stream);
+}
+
+void ph_free(void *handle)
+{
+    if (!handle) return;
+    uint32_t kind = *static_cast<uint32_t *>(handle);
+    if (kind == KIND_LEAVES) {
+        ph_leaves *h = static_cast<ph_leaves *>(handle);
+        free_leaves(h);
+        delete h;
+    } else if (kind == KIND_PAIRS) {
+        ph_pairs *h = static_cast<ph_pairs *>(handle);
+        free_pairs(h);
+        delete h;
+    }
+}
+
+const char *ph_last_error(void) { return g_err; }
+
+int ph_status(const void *handle)
+{
+    if (!handle) return fail(PH_ERR_ARG, "NULL handle");
+    uint32_t kind = *static_cast<const uint32_t *>(handle);
+    if (kind == KIND_LEAVES) {
+        const ph_leaves *h = static_cast<const ph_leaves *>(handle);
+        return read_status(h->status, h->last_stream);
+    }
+    if (kind == KIND_PAIRS) {
+        const ph_pairs *h = static_cast<const ph_pairs *>(handle);
+        return read_status(h->status, h->last_stream);
+    }
+    return fail(PH_ERR_STATE, "unknown handle");
+}
+
+int ph_leaves_get_view(const ph_leaves *h, ph_leaves_view *out)
+{
+    if (!h || h->kind != KIND_LEAVES || !out) return fail(PH_ERR_ARG, "bad arguments");
+    int32_t cnt[2] = {0, 0};
+    int rc = cuda_check(cudaMemcpyAsync(cnt, h->counts.p, 8, cudaMemcpyDeviceToHost, h->last_stream), "read counts");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->last_stream), "view sync");
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->n = h->n;
+    out->n_boxes = h->n_boxes;
+    out->n_leaves = cnt[0];
+    out->n_groups = cnt[1];
+    out->n_cells = h->n_cells;
+    out->keys = static_cast<const uint64_t *>(h->keys_in_alt ? h->keys_alt.p : h->keys.p);
+    out->perm = static_cast<const int32_t *>(h->keys_in_alt ? h->vals_alt.p : h->vals.p);
+    out->leaf_first = static_cast<const int32_t *>(h->leaf_first.p);
+    out->leaf_ref = static_cast<const double *>(h->leaf_ref.p);
+    out->leaf_half = static_cast<const float *>(h->leaf_h4.p);
+    out->group_first = static_cast<const int32_t *>(h->group_first.p);
+    out->group_ref = static_cast<const double *>(h->group_ref.p);
+    out->group_half = static_cast<const float *>(h->group_h4.p);
+    out->pos_leaf = static_cast<const float *>(h->pos_leaf.p);
+    out->pos_group = static_cast<const float *>(h->pos_group.p);
+    out->cell_leaf_first = static_cast<const int32_t *>(h->cell_leaf_first.p);
+    for (int b = 0; b < 4 && b < h->n_boxes; b++) out->g[b] = h->boxes_host[b].g;
+    out->key_bits = h->key_bits;
+    out->group_size = h->group_size;
+    return PH_OK;
+}
+
+int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
+{
+    if (!p || p->kind != KIND_PAIRS || !out || !p->built_from) return fail(PH_ERR_ARG, "bad arguments");
+    const ph_leaves *lv = p->built_from;
+    int32_t ng = 0;
+    int rc = cuda_check(cudaMemcpyAsync(&ng, static_cast<const int32_t *>(lv->counts.p) + 1, 4,
+                                        cudaMemcpyDeviceToHost, p->last_stream),
+                        "read groups");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(p->last_stream), "view sync");
+    int64_t total = 0;
+    if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(&total, static_cast<const int64_t *>(p->group_off.p) + ng, 8,
+                                        cudaMemcpyDeviceToHost, p->last_stream),
+                        "read total");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(p->last_stream), "view sync");
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->n_pairs = total;
+    out->n_groups = ng;
+    out->group_off = static_cast<const int64_t *>(p->group_off.p);
+    out->entries = static_cast<const float *>(p->entries.p);
+    return PH_OK;
+}
+
+int ph_pp_counters(const ph_pairs *p, int64_t *interactions, int64_t *staged)
+{
+    if (!p || p->kind != KIND_PAIRS) return fail(PH_ERR_ARG, "bad arguments");
+    unsigned long long v[3] = {0, 0, 0};
+    int rc = cuda_check(cudaMemcpyAsync(v, p->work.p, 24, cudaMemcpyDeviceToHost, p->last_stream), "read counters");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(p->last_stream), "counter sync");
+    if (rc) return rc;
+    if (interactions) *interactions = (int64_t)v[1];
+    if (staged) *staged = (int64_t)v[2];
+    return PH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,463 @@
+// Tree build on the GPU: keys, sort, leaves, target groups, frames.
+//
+// Sec. 3.2 ("Tree building"): each particle is labelled with its ground cell
+// index (i N_side + j) N_side + k, particles are ordered by that index and,
+// inside a ground cell, by a Morton (or Peano-Hilbert, Sec. 4.1) key, so that
+// every octree node is one contiguous run of particles.  Leaves are the
+// largest octree cells holding at most leaf_max particles (the N_pp of
+// Sec. 3.1, the leaf size of Sec. 4.4).
+//
+// Positions are stored relative to a reference point of their leaf in FP32
+// (the FP64 wrap and the reference points are the only FP64 data on the
+// device), and a second copy relative to the reference point of their target
+// group, derived from the first by one FP32 add of the FP64-computed offset,
+// exactly as the PP kernel shifts source particles, so that a particle seen
+// as target and as source has bitwise the same coordinates.
+#include <cmath>
+
+#include "handles.cuh"
+
+namespace phpp {
+namespace {
+
+__device__ __forceinline__ int find_box(const int32_t *box_first, int nb, int64_t i)
+{
+    int lo = 0, hi = nb - 1;          // largest b with box_first[b] <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (box_first[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L)
+{
+    // x - L floor(x / L), each operation rounded once (no contraction)
+    double f = floor(__ddiv_rn(x, L));
+    return __dsub_rn(x, __dmul_rn(L, f));
+}
+
+__device__ __forceinline__ uint32_t quant_coord(double xw, double S, int T)
+{
+    double q = floor(__dmul_rn(xw, S));
+    double top = (double)((1u << T) - 1u);
+    if (!(q >= 0.0)) q = 0.0;
+    if (q > top) q = top;
+    return (uint32_t)q;
+}
+
+// Spread the low 21 bits of v so that bit k lands on bit 3k.
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t interleave3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+}
+
+// 3-D Hilbert index on a 2^bits grid, after J. Skilling, "Programming the
+// Hilbert curve" (AIP Conf. Proc. 707, 2004): coordinates -> transposed index
+// (undo the per-level inversions/exchanges, Gray code), then bit-interleave.
+__device__ __forceinline__ uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z, int bits)
+{
+    if (bits == 0) return 0;
+    uint32_t X[3] = {x, y, z};
+    const uint32_t M = 1u << (bits - 1);
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    return interleave3(X[0], X[1], X[2]);
+}
+
+__device__ __forceinline__ void load_pos(const void *pos, int pos_type, int64_t i, double &x, double &y, double &z)
+{
+    if (pos_type == PH_F64) {
+        const double *p = static_cast<const double *>(pos) + 3 * i;
+        x = p[0]; y = p[1]; z = p[2];
+    } else {
+        const float *p = static_cast<const float *>(pos) + 3 * i;
+        x = p[0]; y = p[1]; z = p[2];
+    }
+}
+
+__global__ void k_keys(const void *pos, int pos_type, int64_t n, const int32_t *box_first, int nb,
+                       const BoxDev *boxes, int T, int key_kind, uint64_t *keys, int32_t *vals, uint32_t *status)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int bi = find_box(box_first, nb, i);
+        const BoxDev &bx = boxes[bi];
+        double x, y, z;
+        load_pos(pos, pos_type, i, x, y, z);
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            atomicOr(status, ST_NONFINITE);
+            x = y = z = 0.0;
+        }
+        uint32_t qx = quant_coord(wrap_coord(x, bx.L), bx.S, T);
+        uint32_t qy = quant_coord(wrap_coord(y, bx.L), bx.S, T);
+        uint32_t qz = quant_coord(wrap_coord(z, bx.L), bx.S, T);
+        const int b = bx.b;
+        const uint32_t lm = (1u << b) - 1u;
+        uint64_t ground = ((uint64_t)(qx >> b) * bx.nside + (qy >> b)) * bx.nside + (qz >> b);
+        uint64_t local = key_kind == PH_KEY_HILBERT ? hilbert3(qx & lm, qy & lm, qz & lm, b)
+                                                    : interleave3(qx & lm, qy & lm, qz & lm);
+        uint64_t boxbits = 3 * T < 64 ? ((uint64_t)bi << (3 * T)) : 0ull;
+        keys[i] = boxbits | (ground << (3 * b)) | local;
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_gather(const void *pos, int pos_type, const float *mass, int64_t n, const uint64_t *keys,
+                         const int32_t *perm, const BoxDev *boxes, int T, double *xw, float *mass_sorted,
+                         uint32_t *status)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        const int bi = 3 * T < 64 ? (int)(keys[k] >> (3 * T)) : 0;
+        const BoxDev &bx = boxes[bi];
+        double x, y, z;
+        load_pos(pos, pos_type, i, x, y, z);
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = 0.0;
+        xw[3 * k + 0] = wrap_coord(x, bx.L);
+        xw[3 * k + 1] = wrap_coord(y, bx.L);
+        xw[3 * k + 2] = wrap_coord(z, bx.L);
+        float m = mass ? mass[i] : bx.mass_default;
+        if (!isfinite(m)) {
+            atomicOr(status, ST_NONFINITE);
+            m = 0.f;
+        }
+        mass_sorted[k] = m;
+    }
+}
+
+__device__ __forceinline__ int box_of_cell(const BoxDev *boxes, int nb, int c)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].cell_base <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t lo, int64_t hi, uint64_t v)
+{
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_cell_first(const uint64_t *keys, int64_t n, const BoxDev *boxes, int nb, int n_cells, int T,
+                             int32_t *cell_first)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells; c += gridDim.x * blockDim.x) {
+        if (c == n_cells) {
+            cell_first[c] = (int32_t)n;
+            continue;
+        }
+        const int bi = box_of_cell(boxes, nb, c);
+        const BoxDev &bx = boxes[bi];
+        const uint64_t boxbits = 3 * T < 64 ? ((uint64_t)bi << (3 * T)) : 0ull;
+        const uint64_t pre = boxbits | ((uint64_t)(c - bx.cell_base) << (3 * bx.b));
+        cell_first[c] = (int32_t)lower_bound_u64(keys, bx.first, (int64_t)bx.first + bx.n, pre);
+    }
+}
+
+// Leaf and group start flags (see the leaf rule in the file comment).
+__global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, int T, int leaf_max,
+                        const int32_t *cell_first, int32_t *leaf_flag, int32_t *group_flag)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t Bk = keys[k];
+        const int bi = 3 * T < 64 ? (int)(Bk >> (3 * T)) : 0;
+        const BoxDev &bx = boxes[bi];
+        const int b = bx.b;
+        const uint64_t cellpre = Bk >> (3 * b);
+        const int cell = bx.cell_base + (int)(cellpre & ((1ull << (3 * bx.g)) - 1ull));
+        // target groups: runs of group_size inside each ground cell
+        const int64_t cf = cell_first[cell];
+        group_flag[k] = ((k - cf) % bx.group_size) == 0 ? 1 : 0;
+        int lf;
+        if (k == 0) {
+            lf = 1;
+        } else {
+            const uint64_t A = keys[k - 1];
+            if ((A >> (3 * b)) != cellpre || (3 * T < 64 && (A >> (3 * T)) != (Bk >> (3 * T)))) {
+                lf = 1;   // new box or new ground cell
+            } else {
+                const uint64_t x = A ^ Bk;
+                if (x == 0) {
+                    // identical keys: a finest cell; cut into runs of leaf_max
+                    // from its first particle if it is too full
+                    int64_t lo = k - 1, step = 1;
+                    while (lo - step >= 0 && keys[lo - step] == Bk) { lo -= step; step <<= 1; }
+                    int64_t a = lo - step < 0 ? 0 : lo - step;  // keys[a] may or may not equal Bk
+                    lo = lower_bound_u64(keys, a, lo + 1, Bk);
+                    int64_t hi = k, st2 = 1;
+                    while (hi + st2 < n && keys[hi + st2] == Bk) { hi += st2; st2 <<= 1; }
+                    int64_t e = hi + st2 < n ? hi + st2 : n;
+                    hi = lower_bound_u64(keys, hi, e, Bk + 1);   // first index > Bk
+                    lf = (hi - lo > leaf_max && ((k - lo) % leaf_max) == 0) ? 1 : 0;
+                } else {
+                    const int hb = 63 - __clzll((long long)x);
+                    const int sh = 3 * (hb / 3 + 1);        // prefix shift of the common cell
+                    const uint64_t P = Bk >> sh;
+                    // is the common cell (holding k-1 and k) larger than leaf_max?
+                    bool big;
+                    const int64_t far = k - 1 - leaf_max;
+                    if (far >= 0 && (keys[far] >> sh) == P) {
+                        big = true;
+                    } else {
+                        int64_t lo = far < 0 ? 0 : far + 1, hi = k - 1;   // first index with prefix P
+                        while (lo < hi) {
+                            int64_t mid = (lo + hi) >> 1;
+                            if ((keys[mid] >> sh) < P) lo = mid + 1; else hi = mid;
+                        }
+                        const int64_t q = lo + leaf_max;
+                        big = q < n && (keys[q] >> sh) == P;
+                    }
+                    lf = big ? 1 : 0;
+                }
+            }
+        }
+        leaf_flag[k] = lf;
+    }
+}
+
+__global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, int32_t *first)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[k]) first[scan[k]] = (int32_t)k;
+        if (k == n - 1) first[scan[n]] = (int32_t)n;
+    }
+}
+
+// Bounding box of each leaf (or group): FP64 reference point = box centre,
+// FP32 half extents rounded up, FP32 centre relative to the ground cell's
+// lower corner.
+__global__ void k_boxes(const int32_t *first, const int32_t *scan_total, int64_t n, const double *xw,
+                        const uint64_t *keys, const BoxDev *boxes, int T, double *ref, float4 *c4, float4 *h4,
+                        int32_t *cell_of, int32_t *box_of)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int count = *scan_total;
+    for (int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < count; l += warps) {
+        const int a = first[l], e = first[l + 1];
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = a + lane; k < e; k += 32) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                double v = xw[3 * (int64_t)k + d];
+                lo[d] = fmin(lo[d], v);
+                hi[d] = fmax(hi[d], v);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+        }
+        if (lane == 0) {
+            const uint64_t key = keys[a];
+            const int bi = 3 * T < 64 ? (int)(key >> (3 * T)) : 0;
+            const BoxDev &bx = boxes[bi];
+            const uint32_t ground = (uint32_t)((key >> (3 * bx.b)) & ((1ull << (3 * bx.g)) - 1ull));
+            const uint32_t gz = ground % bx.nside, gy = (ground / bx.nside) % bx.nside,
+                           gx = ground / (bx.nside * bx.nside);
+            const double org[3] = {__dmul_rn((double)gx, bx.h), __dmul_rn((double)gy, bx.h),
+                                   __dmul_rn((double)gz, bx.h)};
+            float c[3], hh[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                double r = __dmul_rn(0.5, __dadd_rn(lo[d], hi[d]));
+                double half = __dmul_rn(0.5, __dsub_rn(hi[d], lo[d]));
+                ref[3 * (int64_t)l + d] = r;
+                c[d] = __double2float_rn(__dsub_rn(r, org[d]));
+                hh[d] = __double2float_ru(half);
+            }
+            c4[l] = make_float4(c[0], c[1], c[2], 0.f);
+            h4[l] = make_float4(hh[0], hh[1], hh[2], 0.f);
+            if (cell_of) cell_of[l] = bx.cell_base + (int)ground;
+            if (box_of) box_of[l] = bi;
+        }
+    }
+}
+
+__global__ void k_pos(int64_t n, const double *xw, const float *mass_sorted, const int32_t *leaf_scan,
+                      const int32_t *group_scan, const double *leaf_ref, const double *group_ref, float4 *pos_leaf,
+                      float4 *pos_group)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = leaf_scan[k + 1] - 1;
+        const int64_t g = group_scan[k + 1] - 1;
+        float p[3], q[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double lr = leaf_ref[3 * l + d];
+            p[d] = __double2float_rn(__dsub_rn(xw[3 * k + d], lr));
+            // same FP64 offset and FP32 add as the PP kernel's source shift
+            const float off = __double2float_rn(__dsub_rn(lr, group_ref[3 * g + d]));
+            q[d] = __fadd_rn(p[d], off);
+        }
+        const float m = mass_sorted[k];
+        pos_leaf[k] = make_float4(p[0], p[1], p[2], m);
+        pos_group[k] = make_float4(q[0], q[1], q[2], m);
+    }
+}
+
+__global__ void k_cell_leaf_first(const int32_t *cell_first, const int32_t *leaf_scan, int n_cells,
+                                  int32_t *cell_leaf_first)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells; c += gridDim.x * blockDim.x)
+        cell_leaf_first[c] = leaf_scan[cell_first[c]];
+}
+
+inline int grid_for(int64_t n, int threads = kThreads, int cap = 152 * 16)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+// h(u) = exp(u^2) erfc(u) + 2u/sqrt(pi), so that Eq. (split) is f = exp(-u^2) h(u)
+// with u = s / 2R_s.  Chebyshev interpolation of h on [0, U] at deg+1 nodes,
+// returned as monomial coefficients in t = 2u/U - 1.
+void fit_factor_poly(double U, int deg, float *coef)
+{
+    const int n = deg + 1;
+    double f[kMaxPoly + 1], c[kMaxPoly + 1];
+    for (int k = 0; k < n; k++) {
+        double t = std::cos(M_PI * (k + 0.5) / n);
+        double u = 0.5 * (t + 1.0) * U;
+        f[k] = std::exp(u * u) * std::erfc(u) + 2.0 * u / std::sqrt(M_PI);
+    }
+    for (int j = 0; j < n; j++) {
+        double s = 0.0;
+        for (int k = 0; k < n; k++) s += f[k] * std::cos(j * M_PI * (k + 0.5) / n);
+        c[j] = 2.0 * s / n;
+    }
+    c[0] *= 0.5;
+    // monomial coefficients: sum_j c_j T_j(t), T_{j+1} = 2t T_j - T_{j-1}
+    double m[kMaxPoly + 1] = {0}, Tm1[kMaxPoly + 2] = {0}, T0[kMaxPoly + 2] = {0}, T1[kMaxPoly + 2] = {0};
+    T0[0] = 1.0;                    // T_0
+    for (int j = 0; j < n; j++) {
+        const double *Tj = j == 0 ? T0 : T1;
+        for (int k = 0; k <= j; k++) m[k] += c[j] * Tj[k];
+        if (j == 0) {
+            T1[1] = 1.0;            // T_1 = t
+            for (int k = 0; k <= kMaxPoly; k++) Tm1[k] = T0[k];
+        } else {
+            double Tn[kMaxPoly + 2] = {0};
+            for (int k = 0; k <= j; k++) Tn[k + 1] += 2.0 * T1[k];
+            for (int k = 0; k <= j; k++) Tn[k] -= Tm1[k];
+            for (int k = 0; k <= kMaxPoly; k++) { Tm1[k] = T1[k]; T1[k] = Tn[k]; }
+        }
+    }
+    for (int k = 0; k <= kMaxPoly; k++) coef[k] = k < n ? (float)m[k] : 0.f;
+}
+
+// Enqueue the whole leaf/group build for the particles already in device
+// memory (pos, mass).  The handle's box table and buffers are set up.
+int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float *mass, cudaStream_t s)
+{
+    const int64_t n = h->n;
+    const int nb = h->n_boxes;
+    const int T = h->key_bits;
+    const BoxDev *boxes = static_cast<const BoxDev *>(h->boxes.p);
+    const int32_t *box_first = static_cast<const int32_t *>(h->box_first.p);
+    uint32_t *status = static_cast<uint32_t *>(h->status.p);
+    uint64_t *keys = static_cast<uint64_t *>(h->keys.p);
+    int32_t *vals = static_cast<int32_t *>(h->vals.p);
+    if (n > 0) {
+        k_keys<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, n, box_first, nb, boxes, T, h->key_kind, keys, vals,
+                                               status);
+        bool alt = false;
+        int bits = 3 * T + (nb > 1 ? (int)std::ceil(std::log2((double)nb)) : 0);
+        bits = (bits + kSortBits - 1) / kSortBits * kSortBits;
+        int rc = radix_sort_pairs(keys, vals, static_cast<uint64_t *>(h->keys_alt.p),
+                                  static_cast<int32_t *>(h->vals_alt.p), n, bits, h->temp.p, s, &alt);
+        if (rc) return rc;
+        h->keys_in_alt = alt;
+    } else {
+        h->keys_in_alt = false;
+    }
+    const uint64_t *sk = static_cast<const uint64_t *>(h->keys_in_alt ? h->keys_alt.p : h->keys.p);
+    const int32_t *perm = static_cast<const int32_t *>(h->keys_in_alt ? h->vals_alt.p : h->vals.p);
+    double *xw = static_cast<double *>(h->xw.p);
+    float *ms = static_cast<float *>(h->mass_sorted.p);
+    int32_t *cell_first = static_cast<int32_t *>(h->cell_first.p);
+    int32_t *lflag = static_cast<int32_t *>(h->leaf_flag.p), *gflag = static_cast<int32_t *>(h->group_flag.p);
+    int32_t *lscan = static_cast<int32_t *>(h->leaf_scan.p), *gscan = static_cast<int32_t *>(h->group_scan.p);
+    if (n > 0)
+        k_gather<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, mass, n, sk, perm, boxes, T, xw, ms, status);
+    k_cell_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(sk, n, boxes, nb, h->n_cells, T, cell_first);
+    if (n > 0)
+        k_flags<<<grid_for(n), kThreads, 0, s>>>(sk, n, boxes, T, h->max_leaf, cell_first, lflag, gflag);
+    int rc = scan_exclusive_i32(lflag, lscan, n, nullptr, h->temp.p, s);
+    if (rc) return rc;
+    rc = scan_exclusive_i32(gflag, gscan, n, nullptr, h->temp.p, s);
+    if (rc) return rc;
+    int32_t *lfirst = static_cast<int32_t *>(h->leaf_first.p), *gfirst = static_cast<int32_t *>(h->group_first.p);
+    if (n > 0) {
+        k_firsts<<<grid_for(n), kThreads, 0, s>>>(lflag, lscan, n, lfirst);
+        k_firsts<<<grid_for(n), kThreads, 0, s>>>(gflag, gscan, n, gfirst);
+    } else {
+        cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
+    }
+    const int box_grid = grid_for(n * 32 / 8 + 32);
+    k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
+                                          static_cast<float4 *>(h->leaf_c4.p), static_cast<float4 *>(h->leaf_h4.p),
+                                          nullptr, nullptr);
+    k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, n, xw, sk, boxes, T,
+                                          static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_c4.p),
+                                          static_cast<float4 *>(h->group_h4.p), static_cast<int32_t *>(h->group_cell.p),
+                                          static_cast<int32_t *>(h->group_box.p));
+    if (n > 0)
+        k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
+                                               static_cast<const double *>(h->group_ref.p),
+                                               static_cast<float4 *>(h->pos_leaf.p),
+                                               static_cast<float4 *>(h->pos_group.p));
+    k_cell_leaf_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(cell_first, lscan, h->n_cells,
+                                                                    static_cast<int32_t *>(h->cell_leaf_first.p));
+    // device copies of the counts
+    int32_t *cnt = static_cast<int32_t *>(h->counts.p);
+    cudaMemcpyAsync(cnt + 0, lscan + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(cnt + 1, gscan + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    return cuda_check(cudaGetLastError(), "build kernels");
+}
+
+}  // namespace phpp

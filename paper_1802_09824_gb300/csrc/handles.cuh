@@ -1,0 +1,64 @@
+// Handle layouts (host structs owning device buffers).
+#pragma once
+
+#include <vector>
+
+#include "phpp_internal.cuh"
+
+struct ph_leaves {
+    uint32_t kind = phpp::KIND_LEAVES;
+    cudaStream_t last_stream = nullptr;
+    int64_t n = 0;
+    int32_t n_boxes = 0;
+    int32_t n_cells = 0;
+    int32_t key_bits = 21;       // T
+    int32_t group_size = 32;
+    int32_t poly_degree = 10;
+    int32_t max_leaf = 32;
+    int32_t key_kind = PH_KEY_MORTON;
+    std::vector<phpp::BoxDev> boxes_host;
+    // device buffers
+    phpp::DevBuf boxes;          // BoxDev[n_boxes]
+    phpp::DevBuf box_first;      // int32[n_boxes + 1]  first particle row of each box
+    phpp::DevBuf in_pos;         // staging copy of host positions
+    phpp::DevBuf in_mass;        // staging copy of host masses
+    phpp::DevBuf keys, keys_alt; // uint64[n]
+    phpp::DevBuf vals, vals_alt; // int32[n]
+    phpp::DevBuf xw;             // double[3n] wrapped positions in sorted order
+    phpp::DevBuf mass_sorted;    // float[n]
+    phpp::DevBuf cell_first;     // int32[n_cells + 1]
+    phpp::DevBuf leaf_flag, group_flag;   // int32[n]
+    phpp::DevBuf leaf_scan, group_scan;   // int32[n + 1]
+    phpp::DevBuf leaf_first;     // int32[n + 1]
+    phpp::DevBuf group_first;    // int32[n + 1]
+    phpp::DevBuf leaf_ref;       // double[3 n]
+    phpp::DevBuf leaf_c4, leaf_h4;        // float4[n] (centre in cell frame, half extents)
+    phpp::DevBuf group_ref;      // double[3 n]
+    phpp::DevBuf group_c4, group_h4;      // float4[n]
+    phpp::DevBuf group_cell;     // int32[n] global ground cell of each group
+    phpp::DevBuf group_box;      // int32[n]
+    phpp::DevBuf pos_leaf;       // float4[n]
+    phpp::DevBuf pos_group;      // float4[n]
+    phpp::DevBuf cell_leaf_first;// int32[n_cells + 1]
+    phpp::DevBuf counts;         // int32[4]: n_leaves, n_groups (device copies)
+    phpp::DevBuf status;         // uint32 device status word
+    phpp::DevBuf temp;           // scan / sort scratch
+    bool keys_in_alt = false;
+};
+
+struct ph_pairs {
+    uint32_t kind = phpp::KIND_PAIRS;
+    cudaStream_t last_stream = nullptr;
+    int64_t capacity = 0;        // entries
+    bool fixed_capacity = false;
+    int64_t n_pairs = 0;         // host copy (valid after sizing sync)
+    int32_t n_groups_cap = 0;
+    const ph_leaves *built_from = nullptr;
+    phpp::DevBuf group_cnt;      // int64[n + 1]
+    phpp::DevBuf group_off;      // int64[n + 1]
+    phpp::DevBuf entries;        // float4[capacity]
+    phpp::DevBuf work;           // int32 queue counter + int64 work counters
+    phpp::DevBuf status;         // uint32
+    phpp::DevBuf temp;
+    phpp::DevBuf acc_tmp;        // float[3n] when the caller passes host memory
+};

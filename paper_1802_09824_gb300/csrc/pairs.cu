@@ -1,0 +1,155 @@
+// Cutoff leaf-pair list (CSR by target group).
+//
+// Sec. 4.3: each ground cell is one task that sums over itself and its 26
+// neighbours (the cells are at least R_cut wide, Sec. 3.1, so no pair within
+// R_cut is further away).  Sec. 3.3: leaf-leaf pairs go to the PP kernel.
+// Here the unit on the target side is a group of consecutive particles of one
+// ground cell; for every group the leaves of the 27 cells around it are
+// tested box against box, each neighbour cell with the periodic image its
+// offset implies (with N_side < 3 the same cell appears through several
+// images; at most one of them can be within R_cut < L/2 of any particle).
+//
+// The test runs in FP32 on cell-relative centres with a relative margin on
+// R_cut, so no pair the PP kernel could accept is ever dropped; the stored
+// offset of an accepted pair is computed from the FP64 reference points.
+#include "handles.cuh"
+
+namespace phpp {
+namespace {
+
+struct PairArgs {
+    const BoxDev *boxes;
+    const int32_t *n_groups;
+    const int32_t *group_cell;
+    const int32_t *group_box;
+    const float4 *group_c4, *group_h4;
+    const double *group_ref;
+    const int32_t *cell_leaf_first;
+    const float4 *leaf_c4, *leaf_h4;
+    const double *leaf_ref;
+    int64_t *cnt;            // count pass output [n_groups]
+    const int64_t *off;      // fill pass input   [n_groups + 1]
+    float4 *ent;             // fill pass output
+    int64_t cap;
+    uint32_t *status;
+};
+
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int ng = *a.n_groups;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps) {
+        const BoxDev &bx = a.boxes[a.group_box[g]];
+        const int ns = bx.nside;
+        const int ground = a.group_cell[g] - bx.cell_base;
+        const int gx = ground / (ns * ns), gy = (ground / ns) % ns, gz = ground % ns;
+        const float4 gc = a.group_c4[g], gh = a.group_h4[g];
+        const float hc = (float)bx.h;
+        const float rf2 = bx.rfilt2;
+        double gref[3] = {0, 0, 0};
+        int64_t base = 0;
+        if (kFill) {
+            gref[0] = a.group_ref[3 * (int64_t)g];
+            gref[1] = a.group_ref[3 * (int64_t)g + 1];
+            gref[2] = a.group_ref[3 * (int64_t)g + 2];
+            base = a.off[g];
+        }
+        int64_t count = 0;
+        for (int nb = 0; nb < 27; nb++) {
+            const int dx = nb / 9 - 1, dy = (nb / 3) % 3 - 1, dz = nb % 3 - 1;
+            const int ax = gx + dx, ay = gy + dy, az = gz + dz;
+            const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
+            const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
+            const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+            const int nc = bx.cell_base + ((ax - sx * ns) * ns + (ay - sy * ns)) * ns + (az - sz * ns);
+            const int l0 = a.cell_leaf_first[nc], l1 = a.cell_leaf_first[nc + 1];
+            const float ox = dx * hc, oy = dy * hc, oz = dz * hc;
+            for (int lb = l0; lb < l1; lb += 32) {
+                const int l = lb + lane;
+                bool acc = false;
+                if (l < l1) {
+                    const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
+                    float qx = fmaxf(fabsf((lc.x + ox) - gc.x) - (gh.x + lh.x), 0.f);
+                    float qy = fmaxf(fabsf((lc.y + oy) - gc.y) - (gh.y + lh.y), 0.f);
+                    float qz = fmaxf(fabsf((lc.z + oz) - gc.z) - (gh.z + lh.z), 0.f);
+                    acc = qx * qx + qy * qy + qz * qz < rf2;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                if (kFill && acc) {
+                    const int64_t pos = base + count + __popc(bal & lt);
+                    if (pos < a.cap) {
+                        const double *lr = a.leaf_ref + 3 * (int64_t)l;
+                        const double L = bx.L;
+                        float4 e;
+                        e.x = __double2float_rn((lr[0] + sx * L) - gref[0]);
+                        e.y = __double2float_rn((lr[1] + sy * L) - gref[1]);
+                        e.z = __double2float_rn((lr[2] + sz * L) - gref[2]);
+                        e.w = __int_as_float(l);
+                        a.ent[pos] = e;
+                    } else {
+                        atomicOr(a.status, ST_CAPACITY);
+                    }
+                }
+                count += __popc(bal);
+            }
+        }
+        if (!kFill && lane == 0) a.cnt[g] = count;
+    }
+}
+
+}  // namespace
+
+int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync)
+{
+    PairArgs a;
+    a.boxes = static_cast<const BoxDev *>(lv->boxes.p);
+    a.n_groups = static_cast<const int32_t *>(lv->counts.p) + 1;
+    a.group_cell = static_cast<const int32_t *>(lv->group_cell.p);
+    a.group_box = static_cast<const int32_t *>(lv->group_box.p);
+    a.group_c4 = static_cast<const float4 *>(lv->group_c4.p);
+    a.group_h4 = static_cast<const float4 *>(lv->group_h4.p);
+    a.group_ref = static_cast<const double *>(lv->group_ref.p);
+    a.cell_leaf_first = static_cast<const int32_t *>(lv->cell_leaf_first.p);
+    a.leaf_c4 = static_cast<const float4 *>(lv->leaf_c4.p);
+    a.leaf_h4 = static_cast<const float4 *>(lv->leaf_h4.p);
+    a.leaf_ref = static_cast<const double *>(lv->leaf_ref.p);
+    a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
+    a.off = static_cast<const int64_t *>(pr->group_off.p);
+    a.status = static_cast<uint32_t *>(pr->status.p);
+    const int64_t n = lv->n;
+    const int grid = 152 * 8;
+    k_pairs<false><<<grid, kThreads, 0, s>>>(a);
+    int rc = scan_exclusive_i64(a.cnt, static_cast<int64_t *>(pr->group_off.p), n, a.n_groups, pr->temp.p, s);
+    if (rc) return rc;
+    if (sizing_sync) {
+        // total = group_off[n_groups]; read the count then the total
+        int32_t ng = 0;
+        rc = cuda_check(cudaMemcpyAsync(&ng, a.n_groups, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy n_groups");
+        if (rc) return rc;
+        rc = cuda_check(cudaStreamSynchronize(s), "sync n_groups");
+        if (rc) return rc;
+        int64_t total = 0;
+        rc = cuda_check(cudaMemcpyAsync(&total, static_cast<const int64_t *>(pr->group_off.p) + ng, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s),
+                        "copy pair total");
+        if (rc) return rc;
+        rc = cuda_check(cudaStreamSynchronize(s), "sync pair total");
+        if (rc) return rc;
+        pr->n_pairs = total;
+        if (total > pr->capacity) {
+            int64_t cap = total + total / 8 + 1024;
+            rc = ensure(pr->entries, (size_t)cap * sizeof(float4));
+            if (rc) return rc;
+            pr->capacity = cap;
+        }
+    }
+    a.ent = static_cast<float4 *>(pr->entries.p);
+    a.cap = pr->capacity;
+    k_pairs<true><<<grid, kThreads, 0, s>>>(a);
+    return cuda_check(cudaGetLastError(), "pair kernels");
+}
+
+}  // namespace phpp

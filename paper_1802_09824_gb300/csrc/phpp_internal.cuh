@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libphpp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/phpp.h"
+
+namespace phpp {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxPoly = 16;          // highest degree of the factor polynomial
+constexpr int kMaxLeaf = 256;         // largest leaf_max accepted
+constexpr int kGroundMax = 7;         // N_side <= 2^7 per box
+constexpr int kSortBits = 8;          // radix digit width
+constexpr int kThreads = 256;
+
+// Per-box constants, one record per box in device memory.
+struct BoxDev {
+    double L;          // box side
+    double S;          // 2^T / L: quantisation scale of the key grid
+    double h;          // ground cell side L / N_side
+    float G;
+    float eps2;        // eps^2
+    float rcut2;       // rcut^2 (cutoff decision of the PP kernel)
+    float rfilt2;      // (rcut (1 + margin))^2 for conservative box tests
+    float c_v;         // v = sqrt(r^2 c_v) = r / (R_s U), t = v - 1 in [-1, 1]
+    float c_e;         // exp(-r^2 / 4R_s^2) = 2^(r^2 c_e)
+    float mass_default;
+    int32_t g;         // ground level, N_side = 2^g
+    int32_t b;         // local key bits per axis
+    int32_t nside;
+    int32_t cell_base; // first global ground cell of this box
+    int32_t first;     // first particle row of this box
+    int32_t n;         // particles in this box
+    int32_t group_size;
+    int32_t pad;
+    float poly[kMaxPoly + 1];   // h(t) = sum poly[k] t^k, f = 2^(r^2 c_e) h
+};
+
+// Device-side status word bits.
+enum : uint32_t {
+    ST_NONFINITE = 1u,
+    ST_CAPACITY = 2u,
+    ST_TIMEOUT = 4u,
+};
+
+// ---------------------------------------------------------------- handles
+enum HandleKind : uint32_t { KIND_LEAVES = 0x4c454146u, KIND_PAIRS = 0x50414952u, KIND_MLP = 0x4d4c5021u };
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ph_leaves_impl;
+struct ph_pairs_impl;
+
+// Thread-local error message.
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+
+// Grow a device buffer to at least `bytes` (contents not preserved).
+int ensure(DevBuf &b, size_t bytes);
+void release(DevBuf &b);
+
+// true if `p` is device-accessible memory (device or managed).
+bool is_device_ptr(const void *p);
+
+int cuda_check(cudaError_t e, const char *what);
+
+// ---------------------------------------------------------------- kernels
+// scan.cu: exclusive scans over n elements (n read from device memory when
+// d_n != nullptr, else the host value).  out[n] receives the total.
+size_t scan_temp_bytes(int64_t max_n);
+int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, const int32_t *d_n, void *temp,
+                       cudaStream_t s);
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, const int32_t *d_n, void *temp,
+                       cudaStream_t s);
+
+// sort.cu: stable LSD radix sort of (key, value) pairs on the low `bits` bits.
+size_t sort_temp_bytes(int64_t n);
+int radix_sort_pairs(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int32_t *vals_alt, int64_t n, int bits,
+                     void *temp, cudaStream_t s, bool *result_in_alt);
+
+}  // namespace phpp
