@@ -1,0 +1,352 @@
+"""Benchmark of the short-range PP hot path on GB300.
+
+A step is one pass of the whole path over one particle set already resident
+in HBM: keys + sort + leaves + groups (ph_build_leaves), the cutoff leaf-pair
+list (ph_leaf_pairs) and the exact-factor PP sum (ph_pp_accel).  The default
+workload is the 128^3 Zel'dovich lattice (L=100, rs=1.25 L/128, rcut=4.5 rs,
+eps=L/128/30).
+
+value     = interactions within rcut (ordered pairs j != i, r < rcut) per
+            second of whole-step time, summed over ranks;
+e2e       = the same through one ph_accel call per step with host buffers
+            (positions/masses copied in, accelerations copied out inside the
+            timed region);
+roofline  = the PP kernel's FP32 rate (interactions it evaluated x the stated
+            flop count per interaction / its CUDA-event time) against the FP32
+            FMA peak: SMs x 128 lanes x 2 flop x max SM clock;
+cpu_baseline / --impl reference = the FP64 oracle on the host's cores over a
+            bounded sample of the same workload (all sources, a subset of
+            targets), in the same unit.
+
+With N > 1 (torchrun) each rank runs an independent replica of the workload
+on its own GPU (the path has no exchange step at this size); value is the
+sum over ranks, time the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PP interactions/sec and % of GB300 FP32 peak; learned-g vs exact-g speedup at error"
+UNIT = "interactions/s"
+
+# FP32 operations per evaluated pair in k_pp_exact (counted from the source,
+# FADD/FMUL = 1 flop, FFMA = 2, SFU rsqrt/sqrt/ex2 = 0, Kahan adds and the
+# cutoff select not counted): d 3 FADD; r^2 1 FMUL + 2 FFMA; r^2+eps^2 1 FADD;
+# Newton-corrected (r^2+eps^2)^-3/2 3 FMUL + 2 FFMA; r^2 c_v 1 FMUL; t 1 FADD;
+# degree-10 Horner 10 FFMA; ex2 argument 1 FMUL; f 1 FMUL; w 2 FMUL;
+# accumulation 3 FFMA  ->  5 FADD + 9 FMUL + 17 FFMA = 48 flop.
+FLOPS_PER_INTERACTION = 48
+PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
+# DRAM traffic per PP launch (bytes) from the ncu capture summarised in
+# profiles/pp_exact_zeldovich.md, or None when the kernel changed since.
+PP_TRAFFIC_BYTES = None
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, period_ms=100):
+        self.gpu_index = gpu_index
+        self.period_ms = period_ms
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms", str(self.period_ms), "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() in ("active", "0x1") or v == "1":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    if ids and ids[min(local_rank, len(ids) - 1)].isdigit():
+        return int(ids[min(local_rank, len(ids) - 1)])
+    return local_rank
+
+
+def _params(B, bp, leaf_max, key_kind):
+    return B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max or bp.leaf_max, key_kind)
+
+
+def _oracle_rate(ps, seconds, seed=5):
+    """Oracle over a bounded target sample: (useful interactions/s, targets, s, cores)."""
+    from oracle import force
+    bp = ps.boxes[0]
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    cal = rng.choice(ps.n, 32, replace=False)
+    force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=cal)
+    per_target = (time.perf_counter() - t0) / 32
+    nt = int(min(ps.n, max(32, seconds / max(per_target, 1e-9))))
+    tg = rng.choice(ps.n, nt, replace=False)
+    t0 = time.perf_counter()
+    r = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=tg)
+    dt = time.perf_counter() - t0
+    return float(r.n_within.sum()) / dt, nt, dt, force.num_threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_1802_09824_gb300 import synth
+    ps = synth.workload(args.workload)
+    per_step = max(1.0, args.ref_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        _oracle_rate(ps, 0.2)
+    rates, nts, secs = [], [], []
+    cores = 1
+    for k in range(args.steps):
+        r, nt, dt, cores = _oracle_rate(ps, per_step, seed=100 + k)
+        rates.append(r)
+        nts.append(nt)
+        secs.append(dt)
+    value = float(np.mean(rates))
+    sample = (f"{args.workload}: all {ps.n} sources against {int(np.mean(nts))} random targets per step, "
+              f"FP64 C/OpenMP oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "n": ps.n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1802_09824_gb300 import binding as B
+    from paper_1802_09824_gb300 import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    ps = synth.workload(args.workload)
+    bp = ps.boxes[0]
+    prm = _params(B, bp, args.leaf_max, args.key)
+    pos = torch.from_numpy(ps.pos).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    lv = pr = None
+
+    def step(events=None):
+        nonlocal lv, pr
+        lv = B.ph_build_leaves(pos, mass, prm, stream, leaves=lv)
+        pr = B.ph_leaf_pairs(lv, stream, pairs=pr)
+        if events is not None:
+            events[1].record(stream)
+        B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc, stream)
+        if events is not None:
+            events[2].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    B.ph_status(lv)
+    B.ph_status(pr)
+    n_within = B.ph_count_within(lv, pr, stream)
+    step()
+    torch.cuda.synchronize()
+    computed, staged = B.ph_pp_counters(pr)
+
+    gpu_idx = _gpu_index(local_rank)
+    clocks = ClockSampler(gpu_idx)
+    clocks.start()
+    time.sleep(0.3)
+    # ---- device-resident timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = B.ph_launch_counter()
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between steps (not timed)
+        evs[k][0].record(stream)
+        step(evs[k])
+    barrier()
+    launches = B.ph_launch_counter() - launches0
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    pp_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    t_step = max_over_ranks(sum(step_ms) / args.steps)
+    t_pp = sum(pp_ms) / args.steps
+
+    # ---- end to end through the public call with host buffers
+    pos_h = torch.from_numpy(ps.pos).pin_memory()
+    mass_h = torch.from_numpy(ps.mass).pin_memory()
+    acc_h = torch.empty((ps.n, 3), dtype=torch.float32).pin_memory()
+    lv2 = pr2 = None
+    for _ in range(3):
+        lv2, pr2 = B.ph_accel(pos_h, mass_h, prm, B.PH_G_EXACT, None, acc_h, stream, leaves=lv2, pairs=pr2)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lv2, pr2 = B.ph_accel(pos_h, mass_h, prm, B.PH_G_EXACT, None, acc_h, stream, leaves=lv2, pairs=pr2)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    barrier()
+    clk = clocks.stop()
+    t_e2e = max_over_ranks(sum(e2e_ms) / args.steps)
+    if not np.all(np.isfinite(acc_h.numpy())):
+        raise RuntimeError("non-finite accelerations")
+
+    value = sum_over_ranks(n_within) / (t_step * 1e-3)
+    e2e_value = sum_over_ranks(n_within) / (t_e2e * 1e-3)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                    # TFLOP/s
+    achieved = computed * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": PP_TRAFFIC_BYTES,
+            "kernel": "k_pp_exact", "flops_per_interaction": FLOPS_PER_INTERACTION,
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (peak * clk["sm_mhz"] / sm_max)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": ps.n, "leaf_max": prm.leaf_max,
+                   "key": "hilbert" if args.key else "morton", "group_size": 32,
+                   "l2": "flushed between steps (256 MB write), per-step CUDA events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": t_e2e,
+                "h2d_bytes_per_step": ps.n * 16, "d2h_bytes_per_step": ps.n * 12},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+        "pp": {"ms": t_pp, "interactions_evaluated": computed, "interactions_within_rcut": n_within,
+               "evaluated_per_s": computed / (t_pp * 1e-3), "within_fraction": n_within / max(computed, 1),
+               "staged_sources": staged, "paper_convention_tflops": computed * PAPER_FLOPS_PER_INTERACTION /
+               (t_pp * 1e-3) / 1e12},
+        "build_and_pairs_ms": t_step - t_pp,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, nt, dt, cores = _oracle_rate(ps, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"all {ps.n} sources x {nt} random targets, {dt:.1f} s"}
+    for h in (pr, lv, pr2, lv2):
+        B.ph_free(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zeldovich_128")
+    ap.add_argument("--leaf-max", type=int, default=0)
+    ap.add_argument("--key", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -216,6 +216,16 @@ int ph_pairs_get_view(const ph_pairs *pairs, ph_pairs_view *out);
  * interactions evaluated by the PP kernel, and the j-particles staged. */
 int ph_pp_counters(const ph_pairs *pairs, int64_t *interactions, int64_t *staged);
 
+/* Number of ordered pairs (i, j), j != i, with r_ij < rcut in the lists,
+ * decided in FP32 exactly as ph_pp_accel decides its cutoff: the work the
+ * cutoff keeps (the oracle's count up to pairs within rounding of rcut and
+ * coincident particles).  Synchronises. */
+int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_within, void *stream);
+
+/* Kernel launches the library has issued so far in this process (all
+ * threads); differences around a region count the launches inside it. */
+int64_t ph_launch_counter(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,8 @@ _SIGS = {
     "ph_leaves_get_view": ([_VP, ctypes.POINTER(ph_leaves_view)], ctypes.c_int),
     "ph_pairs_get_view": ([_VP, ctypes.POINTER(ph_pairs_view)], ctypes.c_int),
     "ph_pp_counters": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ph_count_within": ([_VP, _VP, ctypes.POINTER(ctypes.c_int64), _VP], ctypes.c_int),
+    "ph_launch_counter": ([], ctypes.c_int64),
 }
 
 
@@ -242,10 +244,21 @@ def ph_pp_counters(pairs):
     return a.value, b.value
 
 
+def ph_count_within(leaves, pairs, stream=None):
+    """Ordered pairs j != i with r < rcut in the lists (synchronises)."""
+    n = ctypes.c_int64(0)
+    _check(lib().ph_count_within(leaves.ptr, pairs.ptr, ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def ph_launch_counter():
+    return int(lib().ph_launch_counter())
+
+
 # ------------------------------------------------------------ introspection
 class _CudaArray:
     def __init__(self, ptr, shape, typestr):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 2, "strides": None}
 
 

@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, handle management, host/device
 // staging.  Every step of the computation runs in the kernels of build.cu,
 // pairs.cu and pp.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,9 +15,13 @@ namespace phpp {
 int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float *mass, cudaStream_t s);
 int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
+int count_within_device(const ph_leaves *lv, const ph_pairs *pr, cudaStream_t s);
 void fit_factor_poly(double U, int deg, float *coef);
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...)
 {
@@ -515,6 +520,29 @@ int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
     out->entries = static_cast<const float *>(p->entries.p);
     return PH_OK;
 }
+
+int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_within, void *stream)
+{
+    if (!leaves || leaves->kind != KIND_LEAVES || !pairs || pairs->kind != KIND_PAIRS || !n_within)
+        return fail(PH_ERR_ARG, "bad arguments");
+    if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    *n_within = 0;
+    if (leaves->n == 0) return PH_OK;
+    ph_pairs *pr = const_cast<ph_pairs *>(pairs);
+    int rc = count_within_device(leaves, pairs, s);
+    unsigned long long v = 0;
+    if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(&v, static_cast<char *>(pr->work.p) + 8, 8, cudaMemcpyDeviceToHost, s),
+                        "read count");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "count sync");
+    if (rc) return rc;
+    *n_within = (int64_t)v - leaves->n;   // minus the self pairs
+    pr->last_stream = s;
+    return PH_OK;
+}
+
+int64_t ph_launch_counter(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 int ph_pp_counters(const ph_pairs *p, int64_t *interactions, int64_t *staged)
 {

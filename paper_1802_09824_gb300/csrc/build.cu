@@ -259,9 +259,9 @@ __global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, in
     }
 }
 
-// Bounding box of each leaf (or group): FP64 reference point = box centre,
-// FP32 half extents rounded up, FP32 centre relative to the ground cell's
-// lower corner.
+// Bounding box of each leaf (or group): FP64 reference point near the box
+// centre, FP32 half extents around it rounded up, FP32 reference point
+// relative to the ground cell's lower corner.
 __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, int64_t n, const double *xw,
                         const uint64_t *keys, const BoxDev *boxes, int T, double *ref, float4 *c4, float4 *h4,
                         int32_t *cell_of, int32_t *box_of)
@@ -300,8 +300,15 @@ __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, int64_t
             float c[3], hh[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                double r = __dmul_rn(0.5, __dadd_rn(lo[d], hi[d]));
-                double half = __dmul_rn(0.5, __dsub_rn(hi[d], lo[d]));
+                // reference point: the box centre snapped to a multiple of the
+                // FP32 spacing of the box's largest coordinate, so that the
+                // FP32 difference of any FP32 coordinate in it is exact
+                const double mx = fmax(fabs(lo[d]), fabs(hi[d]));
+                int ex;
+                frexp(mx, &ex);
+                const double cen = __dmul_rn(0.5, __dadd_rn(lo[d], hi[d]));
+                const double r = ldexp(rint(ldexp(cen, 24 - ex)), ex - 24);   // exact scalings
+                const double half = fmax(__dsub_rn(hi[d], r), __dsub_rn(r, lo[d]));
                 ref[3 * (int64_t)l + d] = r;
                 c[d] = __double2float_rn(__dsub_rn(r, org[d]));
                 hh[d] = __double2float_ru(half);
@@ -404,6 +411,7 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     if (n > 0) {
         k_keys<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, n, box_first, nb, boxes, T, h->key_kind, keys, vals,
                                                status);
+        count_launch();
         bool alt = false;
         int bits = 3 * T + (nb > 1 ? (int)std::ceil(std::log2((double)nb)) : 0);
         bits = (bits + kSortBits - 1) / kSortBits * kSortBits;
@@ -423,9 +431,12 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     int32_t *lscan = static_cast<int32_t *>(h->leaf_scan.p), *gscan = static_cast<int32_t *>(h->group_scan.p);
     if (n > 0)
         k_gather<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, mass, n, sk, perm, boxes, T, xw, ms, status);
+        count_launch();
     k_cell_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(sk, n, boxes, nb, h->n_cells, T, cell_first);
+    count_launch();
     if (n > 0)
         k_flags<<<grid_for(n), kThreads, 0, s>>>(sk, n, boxes, T, h->max_leaf, cell_first, lflag, gflag);
+        count_launch();
     int rc = scan_exclusive_i32(lflag, lscan, n, nullptr, h->temp.p, s);
     if (rc) return rc;
     rc = scan_exclusive_i32(gflag, gscan, n, nullptr, h->temp.p, s);
@@ -433,7 +444,9 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     int32_t *lfirst = static_cast<int32_t *>(h->leaf_first.p), *gfirst = static_cast<int32_t *>(h->group_first.p);
     if (n > 0) {
         k_firsts<<<grid_for(n), kThreads, 0, s>>>(lflag, lscan, n, lfirst);
+        count_launch();
         k_firsts<<<grid_for(n), kThreads, 0, s>>>(gflag, gscan, n, gfirst);
+        count_launch();
     } else {
         cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
         cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
@@ -442,17 +455,21 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
                                           static_cast<float4 *>(h->leaf_c4.p), static_cast<float4 *>(h->leaf_h4.p),
                                           nullptr, nullptr);
+    count_launch();
     k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, n, xw, sk, boxes, T,
                                           static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_c4.p),
                                           static_cast<float4 *>(h->group_h4.p), static_cast<int32_t *>(h->group_cell.p),
                                           static_cast<int32_t *>(h->group_box.p));
+    count_launch();
     if (n > 0)
         k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
                                                static_cast<const double *>(h->group_ref.p),
                                                static_cast<float4 *>(h->pos_leaf.p),
                                                static_cast<float4 *>(h->pos_group.p));
+        count_launch();
     k_cell_leaf_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(cell_first, lscan, h->n_cells,
                                                                     static_cast<int32_t *>(h->cell_leaf_first.p));
+    count_launch();
     // device copies of the counts
     int32_t *cnt = static_cast<int32_t *>(h->counts.p);
     cudaMemcpyAsync(cnt + 0, lscan + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);

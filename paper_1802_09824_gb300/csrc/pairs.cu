@@ -122,6 +122,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     const int64_t n = lv->n;
     const int grid = 152 * 8;
     k_pairs<false><<<grid, kThreads, 0, s>>>(a);
+    count_launch();
     int rc = scan_exclusive_i64(a.cnt, static_cast<int64_t *>(pr->group_off.p), n, a.n_groups, pr->temp.p, s);
     if (rc) return rc;
     if (sizing_sync) {
@@ -149,6 +150,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.ent = static_cast<float4 *>(pr->entries.p);
     a.cap = pr->capacity;
     k_pairs<true><<<grid, kThreads, 0, s>>>(a);
+    count_launch();
     return cuda_check(cudaGetLastError(), "pair kernels");
 }
 

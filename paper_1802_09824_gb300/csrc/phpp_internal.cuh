@@ -71,6 +71,9 @@ bool is_device_ptr(const void *p);
 
 int cuda_check(cudaError_t e, const char *what);
 
+// Host-side count of kernel launches issued by the library (all threads).
+void count_launch(int n = 1);
+
 // ---------------------------------------------------------------- kernels
 // scan.cu: exclusive scans over n elements (n read from device memory when
 // d_n != nullptr, else the host value).  out[n] receives the total.

@@ -12,8 +12,8 @@
 // Per pair (Eq. (split), Plummer factor, hard cutoff):
 //   r2 = |d|^2,  w = m_j f(r) / (r2 + eps^2)^{3/2}  if r2 < rcut^2 else 0
 //   f(r) = 2^(r2 c_e) h(t),  t = r / (R_s U) - 1,  h a degree-NPOLY polynomial
-// with rsqrt, sqrt and ex2 on the SFU.  Partial sums over one buffer are
-// added to the running total with Kahan compensation.
+// with rsqrt (plus one Newton correction), sqrt and ex2 on the SFU.  Partial
+// sums over runs of 16 sources are added to the total with Kahan compensation.
 #include "handles.cuh"
 
 namespace phpp {
@@ -74,30 +74,54 @@ struct Kahan3 {
     }
 };
 
+// One pair: accumulate m_j f(r) d / (r^2 + eps^2)^{3/2} into (px, py, pz).
+template <int NPOLY>
+__device__ __forceinline__ void interact(const float4 pj, const float4 xi, const float *poly, float eps2, float rcut2,
+                                         float c_v, float c_e, float &px, float &py, float &pz)
+{
+    const float dx = pj.x - xi.x, dy = pj.y - xi.y, dz = pj.z - xi.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    // (r2 + eps2)^(-3/2): SFU rsqrt y, then the first-order Newton
+    // correction y^3 (1 + 3/2 (1 - x y^2)), which removes the SFU error
+    const float x = r2 + eps2;
+    const float y = rsqrt_sfu(x);
+    const float y2 = y * y;
+    const float y3 = y2 * y;
+    const float e15 = fmaf(x * -1.5f, y2, 1.5f);
+    const float inv3 = fmaf(y3, e15, y3);
+    const float t = sqrt_sfu(r2 * c_v) - 1.f;
+    float hp = poly[NPOLY];
+#pragma unroll
+    for (int q = NPOLY - 1; q >= 0; q--) hp = fmaf(hp, t, poly[q]);
+    const float f = ex2_sfu(r2 * c_e) * hp;
+    float w = (pj.w * f) * inv3;
+    w = r2 < rcut2 ? w : 0.f;
+    px = fmaf(w, dx, px);
+    py = fmaf(w, dy, py);
+    pz = fmaf(w, dz, pz);
+}
+
+// Sum a staged buffer: plain FP32 partial sums over runs of kChunk sources,
+// each run added to the total with Kahan compensation.
+constexpr int kChunk = 16;
+
 template <int NPOLY>
 __device__ __forceinline__ void sum_buffer(const float4 *buf, int nbuf, const float4 xi, const float *poly,
                                            float eps2, float rcut2, float c_v, float c_e, Kahan3 &k)
 {
-    float px = 0.f, py = 0.f, pz = 0.f;
-#pragma unroll 2
-    for (int jj = 0; jj < nbuf; jj++) {
-        const float4 pj = buf[jj];
-        const float dx = pj.x - xi.x, dy = pj.y - xi.y, dz = pj.z - xi.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float inv = rsqrt_sfu(r2 + eps2);
-        const float inv3 = inv * inv * inv;
-        const float t = sqrt_sfu(r2 * c_v) - 1.f;
-        float hp = poly[NPOLY];
-#pragma unroll
-        for (int q = NPOLY - 1; q >= 0; q--) hp = fmaf(hp, t, poly[q]);
-        const float f = ex2_sfu(r2 * c_e) * hp;
-        float w = (pj.w * f) * inv3;
-        w = r2 < rcut2 ? w : 0.f;
-        px = fmaf(w, dx, px);
-        py = fmaf(w, dy, py);
-        pz = fmaf(w, dz, pz);
+    int jj = 0;
+    for (; jj + kChunk <= nbuf; jj += kChunk) {
+        float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll 4
+        for (int u = 0; u < kChunk; u++)
+            interact<NPOLY>(buf[jj + u], xi, poly, eps2, rcut2, c_v, c_e, px, py, pz);
+        k.add(px, py, pz);
     }
-    k.add(px, py, pz);
+    if (jj < nbuf) {
+        float px = 0.f, py = 0.f, pz = 0.f;
+        for (; jj < nbuf; jj++) interact<NPOLY>(buf[jj], xi, poly, eps2, rcut2, c_v, c_e, px, py, pz);
+        k.add(px, py, pz);
+    }
 }
 
 template <int NPOLY>
@@ -176,6 +200,58 @@ __global__ void __launch_bounds__(kPPThreads, 4) k_pp_exact(PPArgs a)
     }
 }
 
+// Number of (i, j) pairs with r^2 < rcut^2 in the lists, self pairs
+// included (each target meets itself once, at d = 0): the work the cutoff
+// keeps, counted with the PP kernel's own FP32 decision.
+__global__ void __launch_bounds__(kPPThreads) k_count_within(PPArgs a)
+{
+    __shared__ float4 sbuf[kPPWarps][kJBuf];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    float4 *buf = sbuf[w];
+    const int ng = *a.n_groups;
+    unsigned long long cnt_within = 0;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(a.queue, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const int i0 = a.group_first[g], ni = a.group_first[g + 1] - i0;
+        const BoxDev &bx = a.boxes[a.group_box[g]];
+        const float rcut2 = bx.rcut2;
+        const float4 xi = lane < ni ? a.pos_group[i0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
+        for (int64_t e = a.group_off[g]; e < e1; e++) {
+            const float4 ent = a.entries[e];
+            const int leaf = __float_as_int(ent.w);
+            const int j1 = a.leaf_first[leaf + 1];
+            for (int jb = a.leaf_first[leaf]; jb < j1; jb += 32) {
+                const int j = jb + lane;
+                const bool ok = j < j1;
+                float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ok) {
+                    p = a.pos_leaf[j];
+                    p.x = __fadd_rn(p.x, ent.x);
+                    p.y = __fadd_rn(p.y, ent.y);
+                    p.z = __fadd_rn(p.z, ent.z);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                __syncwarp();
+                if (ok) buf[__popc(bal & lt)] = p;
+                __syncwarp();
+                const int nb = __popc(bal);
+                for (int jj = 0; jj < nb; jj++) {
+                    const float4 pj = buf[jj];
+                    const float dx = pj.x - xi.x, dy = pj.y - xi.y, dz = pj.z - xi.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (lane < ni && r2 < rcut2) cnt_within++;
+                }
+            }
+        }
+    }
+    if (cnt_within) atomicAdd(a.n_inter, cnt_within);
+}
+
 int sm_count()
 {
     static int n = 0;
@@ -190,9 +266,21 @@ int sm_count()
 
 }  // namespace
 
-int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)
+static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArgs &a);
+
+int count_within_device(const ph_leaves *lv, const ph_pairs *pr, cudaStream_t s)
 {
     PPArgs a;
+    pp_args(lv, pr, nullptr, a);
+    int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
+    if (rc) return rc;
+    k_count_within<<<sm_count() * 4, kPPThreads, 0, s>>>(a);
+    count_launch();
+    return cuda_check(cudaGetLastError(), "count kernel");
+}
+
+static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArgs &a)
+{
     a.boxes = static_cast<const BoxDev *>(lv->boxes.p);
     a.n_groups = static_cast<const int32_t *>(lv->counts.p) + 1;
     a.group_first = static_cast<const int32_t *>(lv->group_first.p);
@@ -210,14 +298,20 @@ int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaS
     a.n_inter = reinterpret_cast<unsigned long long *>(work + 8);
     a.n_staged = reinterpret_cast<unsigned long long *>(work + 16);
     a.acc = d_acc;
-    int rc = cuda_check(cudaMemsetAsync(work, 0, 24, s), "reset work queue");
+}
+
+int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)
+{
+    PPArgs a;
+    pp_args(lv, pr, d_acc, a);
+    int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
     const int grid = sm_count() * 4;
     switch (lv->poly_degree) {
-    case 10: k_pp_exact<10><<<grid, kPPThreads, 0, s>>>(a); break;
-    case 12: k_pp_exact<12><<<grid, kPPThreads, 0, s>>>(a); break;
-    case 14: k_pp_exact<14><<<grid, kPPThreads, 0, s>>>(a); break;
-    case 16: k_pp_exact<16><<<grid, kPPThreads, 0, s>>>(a); break;
+    case 10: k_pp_exact<10><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 12: k_pp_exact<12><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 14: k_pp_exact<14><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 16: k_pp_exact<16><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
     default: return fail(PH_ERR_STATE, "unsupported polynomial degree %d", lv->poly_degree);
     }
     return cuda_check(cudaGetLastError(), "pp kernel");

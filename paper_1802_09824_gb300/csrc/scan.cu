@@ -123,8 +123,11 @@ int scan_impl(const T *in, T *out, int64_t n, const int32_t *d_n, void *temp, cu
     T *partial = static_cast<T *>(temp);
     int nb = kScanBlocks;
     k_reduce<T><<<nb, kScanThreads, 0, s>>>(in, n, d_n, partial);
+    count_launch();
     k_scan_partials<T><<<1, kScanThreads, 0, s>>>(partial, nb);
+    count_launch();
     k_scan<T><<<nb, kScanThreads, 0, s>>>(in, out, n, d_n, partial);
+    count_launch();
     return cuda_check(cudaGetLastError(), "scan launch");
 }
 

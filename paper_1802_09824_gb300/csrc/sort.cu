@@ -118,9 +118,11 @@ int radix_sort_pairs(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int32_t 
     bool alt = false;
     for (int shift = 0; shift < bits; shift += kSortBits) {
         k_hist<<<ntiles, kSortThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+        count_launch();
         int rc = scan_exclusive_i32(hist, offs, (int64_t)kBins * ntiles, nullptr, scan_tmp, s);
         if (rc) return rc;
         k_scatter<<<ntiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, offs, ntiles);
+        count_launch();
         std::swap(kin, kout);
         std::swap(vin, vout);
         alt = !alt;

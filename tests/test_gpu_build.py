@@ -24,6 +24,13 @@ def _set(n=3000, seed=11, clustered=False, L=1.0):
     return synth._single(p, np.full(n, 1.0 / n, np.float32), bp, "t")
 
 
+def _snapped(centre, half):
+    lo, hi = centre - half, centre + half
+    U = np.ldexp(1.0, np.frexp(np.maximum(np.abs(lo), np.abs(hi)))[1] - 24)
+    ref = np.rint(centre / U) * U
+    return ref, np.maximum(hi - ref, ref - lo)
+
+
 def _build(B, ps, kind=0, leaf_max=16):
     import torch
     bp = ps.boxes[0]
@@ -47,12 +54,13 @@ def test_keys_sort_leaves_groups_bit_exact(gpu_lib, kind, clustered, n):
     np.testing.assert_array_equal(v["perm"].cpu().numpy(), t.order)
     np.testing.assert_array_equal(v["leaf_first"].cpu().numpy(), t.leaf_first)
     np.testing.assert_array_equal(v["group_first"].cpu().numpy(), t.group_first)
-    # reference points = bounding-box centres (same FP64 operations)
-    lc, lh = t.leaf_boxes()
+    # reference points: box centres snapped to the FP32 spacing of the box's
+    # largest coordinate
+    lc, lh = _snapped(*t.leaf_boxes())
     np.testing.assert_array_equal(v["leaf_ref"].cpu().numpy(), lc)
     half = v["leaf_half"].cpu().numpy()[:, :3].astype(np.float64)
     assert np.all(half >= lh) and np.all(half <= lh * (1 + 2 ** -23) + 1e-300)
-    gc, gh = t.group_boxes()
+    gc, gh = _snapped(*t.group_boxes())
     np.testing.assert_array_equal(v["group_ref"].cpu().numpy(), gc)
     # leaf-relative FP32 positions: one rounding of the FP64 difference
     pl = v["pos_leaf"].cpu().numpy()
@@ -90,8 +98,8 @@ def test_pair_list_matches_box_relation(gpu_lib, clustered, L, rcut):
     v = B.ph_leaves_get_view(lv)
     pv = B.ph_pairs_get_view(pr)
     t = T.BoxTree(ps.pos, L, rcut, 16, 32, 0, T=v["key_bits"])
-    lc, _ = t.leaf_boxes()
-    gc, _ = t.group_boxes()
+    lc, _ = _snapped(*t.leaf_boxes())
+    gc, _ = _snapped(*t.group_boxes())
     off = pv["group_off"].cpu().numpy()
     ent = pv["entries"].cpu().numpy()
     leaf = ent[:, 3].view(np.int32)

@@ -149,3 +149,19 @@ def test_zeldovich_128_full_size_sampled(gpu_lib):
     print(f"zeldovich 128^3 sampled p99 {q:.2e} max {m:.2e}")
     gpu_lib.ph_free(pr)
     gpu_lib.ph_free(lv)
+
+
+def test_count_within_matches_oracle(gpu_lib):
+    B = gpu_lib
+    for ps in (synth.workload("uniform_small"), synth.workload("nfw_mix_256", scale=24)):
+        got, lv, pr = gpu_accel(B, ps)
+        n = B.ph_count_within(lv, pr)
+        ref = oracle_accel(ps, box=0)
+        exp = int(ref.n_within.sum())
+        # pairs within FP32 rounding of rcut may be counted either way
+        near = int(np.sum(ref.near_abs > 0))
+        assert abs(n - exp) <= near, (n, exp, near)
+        ev, st = B.ph_pp_counters(pr)
+        assert ev >= n + ps.n and st > 0
+        B.ph_free(pr)
+        B.ph_free(lv)
