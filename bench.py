@@ -138,9 +138,10 @@ def _oracle_rate(ps, seconds, seed=5):
     bp = ps.boxes[0]
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
-    cal = rng.choice(ps.n, 32, replace=False)
+    ncal = min(ps.n, 256)
+    cal = rng.choice(ps.n, ncal, replace=False)
     force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=cal)
-    per_target = (time.perf_counter() - t0) / 32
+    per_target = (time.perf_counter() - t0) / ncal
     nt = int(min(ps.n, max(32, seconds / max(per_target, 1e-9))))
     tg = rng.choice(ps.n, nt, replace=False)
     t0 = time.perf_counter()
@@ -153,7 +154,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     from paper_1802_09824_gb300 import synth
-    ps = synth.workload(args.workload)
+    ps = synth.workload(args.workload, scale=args.scale or None)
     per_step = max(1.0, args.ref_seconds / max(1, args.steps))
     for _ in range(args.warmup):
         _oracle_rate(ps, 0.2)
@@ -209,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
-    ps = synth.workload(args.workload)
+    ps = synth.workload(args.workload, scale=args.scale or None)
     bp = ps.boxes[0]
     prm = _params(B, bp, args.leaf_max, args.key)
     pos = torch.from_numpy(ps.pos).to(dev)
@@ -299,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": ps.n, "leaf_max": prm.leaf_max,
+        "config": {"workload": args.workload + (f"@{args.scale}" if args.scale else ""), "n": ps.n, "leaf_max": prm.leaf_max,
                    "key": "hilbert" if args.key else "morton", "group_size": 32,
                    "l2": "flushed between steps (256 MB write), per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -333,6 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zeldovich_128")
+    ap.add_argument("--scale", type=int, default=0, help="side count of a smaller lattice (profiling)")
     ap.add_argument("--leaf-max", type=int, default=0)
     ap.add_argument("--key", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
