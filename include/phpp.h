@@ -222,6 +222,42 @@ int ph_pp_counters(const ph_pairs *pairs, int64_t *interactions, int64_t *staged
  * coincident particles).  Synchronises. */
 int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_within, void *stream);
 
+/* ------------------------------------------------------------ no allocation
+ * ph_accel_noalloc -- the whole step (ph_accel with the exact factor) for
+ * one small box, without allocating anything.
+ *
+ * The paper has no counterpart: this exists for callers that must not
+ * allocate device memory themselves, e.g. an application that gives every
+ * library a fixed device-memory budget through its own allocator, or a
+ * latency-critical loop that cannot take the device-wide synchronisation
+ * that cudaMalloc and cudaFree imply.  The caller owns the inputs and the
+ * output; all intermediate data live in one fixed array of
+ * PH_NOALLOC_SCRATCH_BYTES that every GPU which loads libphpp.so holds until
+ * the process exits.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.
+ *
+ *   d_pos   [n*3] device float32 positions (any real coordinates; wrapped).
+ *   d_mass  [n]   device float32 masses, or NULL for 1/n each.
+ *   n       0 .. PH_NOALLOC_MAX_N; larger n returns PH_ERR_ARG.
+ *   params  as for ph_build_leaves; L/rcut must give at most
+ *           PH_NOALLOC_MAX_CELLS ground cells (else PH_ERR_ARG).
+ *   d_acc   [n*3] device float32 output, caller order.
+ * The call synchronises `stream` once before returning.  PH_ERR_CAPACITY
+ * means the leaf-pair list needed more than PH_NOALLOC_PAIRS_PER_PARTICLE
+ * entries per particle (strongly clustered input): use ph_accel instead.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call on a device uses the same array and overwrites what the previous call
+ * left there, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them.
+ */
+#define PH_NOALLOC_MAX_N               16384
+#define PH_NOALLOC_MAX_CELLS           4096
+#define PH_NOALLOC_PAIRS_PER_PARTICLE  32
+#define PH_NOALLOC_SCRATCH_BYTES       (16u << 20)
+int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t n, const ph_params *params,
+                     float *d_acc, void *stream);
+
 /* Kernel launches the library has issued so far in this process (all
  * threads); differences around a region count the launches inside it. */
 int64_t ph_launch_counter(void);

@@ -81,6 +81,7 @@ _SIGS = {
     "ph_pp_counters": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ph_count_within": ([_VP, _VP, ctypes.POINTER(ctypes.c_int64), _VP], ctypes.c_int),
     "ph_launch_counter": ([], ctypes.c_int64),
+    "ph_accel_noalloc": ([_VP, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), _VP, _VP], ctypes.c_int),
 }
 
 
@@ -249,6 +250,13 @@ def ph_count_within(leaves, pairs, stream=None):
     n = ctypes.c_int64(0)
     _check(lib().ph_count_within(leaves.ptr, pairs.ptr, ctypes.byref(n), _stream(stream)))
     return n.value
+
+
+def ph_accel_noalloc(pos, mass, params, acc, stream=None):
+    """Whole exact-factor step for one small box using only the library's
+    fixed scratch array (no device allocation); device tensors only."""
+    return _check(lib().ph_accel_noalloc(_ptr(pos), _ptr(mass), int(pos.shape[0]), ctypes.byref(params),
+                                         _ptr(acc), _stream(stream)))
 
 
 def ph_launch_counter():
