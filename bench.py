@@ -50,7 +50,7 @@ UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 48
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic per PP launch (bytes) from the ncu capture summarised in
-# profiles/pp_exact_zeldovich.md, or None when the kernel changed since.
+# profiles/pp_exact_zeldovich64.md, or None when the kernel changed since.
 PP_TRAFFIC_BYTES = None
 
 
