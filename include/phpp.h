@@ -80,8 +80,13 @@ extern "C" {
  *   leaf_max  largest number of particles in an octree leaf, 1..256 (the
  *             N_pp of Sec. 3.1 / leaf size of Sec. 4.4).
  *   key_kind  PH_KEY_MORTON or PH_KEY_HILBERT.
- *   group_size number of target particles summed together by one set of
- *             lanes: 0 (default, 32), 8, 16, 32 or 64.
+ *   group_size number of target particles summed together by one warp:
+ *             0 (default) or 32.
+ *   level_bits key bits per level of the leaf hierarchy: 3 = octree cells
+ *             (each level splits a cell into 8 children, Sec. 3.2), 1 = the
+ *             same tree with every octree level split into three binary
+ *             levels along the key's x, y, z bits (leaves closer to
+ *             leaf_max); 0 = default (1).
  */
 typedef struct ph_params {
     double  L;
@@ -92,7 +97,7 @@ typedef struct ph_params {
     int32_t leaf_max;
     int32_t key_kind;
     int32_t group_size;
-    int32_t reserved;
+    int32_t level_bits;
 } ph_params;
 
 typedef struct ph_leaves ph_leaves;   /* sorted particles + leaf / group tables */
@@ -101,10 +106,11 @@ typedef struct ph_mlp    ph_mlp;      /* learned short-range factor             
 
 /*
  * Sort the particles of one box along the space-filling curve and cut them
- * into octree leaves and target groups (Sec. 3.2, "Tree building": ground
- * cell index (i N_side + j) N_side + k, bucket order of ground cells, Morton
- * order inside; leaves are the largest octree cells holding <= leaf_max
- * particles, Sec. 3.1 / 4.4).
+ * into leaves and target groups (Sec. 3.2, "Tree building": ground cell
+ * index (i N_side + j) N_side + k, bucket order of ground cells, Morton
+ * order inside; leaves are the largest cells of the tree -- octree cells, or
+ * their binary sub-levels, see level_bits -- holding <= leaf_max particles,
+ * Sec. 3.1 / 4.4).
  *
  *   pos       [n*3] host or device; pos_type PH_F32 or PH_F64; xyz per row.
  *   mass      [n]   host or device float32, or NULL for equal masses 1/n.

@@ -5,9 +5,11 @@ Test infrastructure only.
 * Sort (Sec. 3.2): particles ordered by key, ties by original index.
 * Leaves (Sec. 3.1 N_pp, Sec. 3.2, Sec. 4.4): starting from each ground cell
   (the root of a local octree), a cell holding at most ``leaf_max`` particles
-  is a leaf; a larger one is split into its 8 children (next 3 key bits).  A
-  cell at the finest key level that still holds more than ``leaf_max``
-  particles (coincident keys) is cut into consecutive runs of ``leaf_max``.
+  is a leaf; a larger one is split into its children, the cells of the next
+  ``level_bits`` key bits (3: the 8 octree children; 1: the two halves, so
+  that every octree level becomes three binary levels).  A cell at the
+  finest key level that still holds more than ``leaf_max`` particles
+  (coincident keys) is cut into consecutive runs of ``leaf_max``.
 * i-groups: within each ground cell, consecutive runs of ``group_size``
   sorted particles (the last run of a cell may be shorter).
 * Pair relation (Sec. 3.3 leaf-leaf PP, Sec. 4.3 a ground cell and its 26
@@ -26,11 +28,12 @@ from . import keys as K
 class BoxTree:
     """Oracle tree of one periodic box."""
 
-    def __init__(self, pos, L, rcut, leaf_max, group_size=32, key_kind=0, T=21, box_index=0):
+    def __init__(self, pos, L, rcut, leaf_max, group_size=32, key_kind=0, T=21, box_index=0, level_bits=1):
         pos = np.asarray(pos, np.float64)
         n = pos.shape[0]
         self.L, self.rcut, self.T = float(L), float(rcut), T
         self.leaf_max, self.group_size = int(leaf_max), int(group_size)
+        self.level_bits = int(level_bits)
         key, g, b = K.particle_keys(pos, L, rcut, T, key_kind, box_index)
         self.g, self.b = g, b
         self.nside = 1 << g
@@ -59,11 +62,12 @@ class BoxTree:
         if cnt <= self.leaf_max:
             self.leaf_first.append(lo)
             return
-        if level == self.b:
+        used = level * self.level_bits          # local key bits fixed so far
+        if used >= 3 * self.b:
             for a in range(lo, hi, self.leaf_max):
                 self.leaf_first.append(a)
             return
-        sh = np.uint64(3 * (self.b - level - 1))
+        sh = np.uint64(3 * self.b - used - self.level_bits)
         pref = (self.keys[lo:hi] >> sh).astype(np.int64)
         cut = np.flatnonzero(pref[1:] != pref[:-1]) + 1
         bounds = np.r_[0, cut, cnt] + lo

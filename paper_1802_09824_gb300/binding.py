@@ -41,7 +41,7 @@ class PhError(RuntimeError):
 class ph_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("G", ctypes.c_double), ("eps", ctypes.c_double),
                 ("rs", ctypes.c_double), ("rcut", ctypes.c_double), ("leaf_max", ctypes.c_int32),
-                ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("level_bits", ctypes.c_int32)]
 
 
 class ph_leaves_view(ctypes.Structure):
@@ -137,9 +137,9 @@ def _pos_type(t):
     raise TypeError("positions must be float32 or float64")
 
 
-def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0):
+def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0, level_bits=0):
     return ph_params(float(L), float(G), float(eps), float(rs), float(rcut), int(leaf_max), int(key_kind),
-                     int(group_size), 0)
+                     int(group_size), int(level_bits))
 
 
 class Handle:

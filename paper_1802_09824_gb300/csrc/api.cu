@@ -121,6 +121,8 @@ static int check_params(const ph_params &p, int b)
     if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT)
         return fail(PH_ERR_ARG, "box %d: unknown key_kind %d", b, p.key_kind);
     if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "box %d: group_size must be 0 or 32", b);
+    if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3)
+        return fail(PH_ERR_ARG, "box %d: level_bits must be 0, 1 or 3", b);
     if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
         return fail(PH_ERR_ARG, "box %d: rcut/rs = %g above the supported 9.2", b, p.rcut / p.rs);
     return PH_OK;
@@ -160,8 +162,8 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         int rc = check_params(params[b], b);
         if (rc) return rc;
         if (params[b].leaf_max != params[0].leaf_max || params[b].key_kind != params[0].key_kind ||
-            params[b].group_size != params[0].group_size)
-            return fail(PH_ERR_ARG, "leaf_max, key_kind and group_size must be the same for all boxes");
+            params[b].group_size != params[0].group_size || params[b].level_bits != params[0].level_bits)
+            return fail(PH_ERR_ARG, "leaf_max, key_kind, group_size and level_bits must be the same for all boxes");
     }
     ph_leaves *h = *leaves;
     if (h && h->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "handle is not a ph_leaves");
@@ -178,6 +180,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->max_leaf = params[0].leaf_max;
     h->key_kind = params[0].key_kind;
     h->group_size = params[0].group_size ? params[0].group_size : 32;
+    h->level_bits = params[0].level_bits ? params[0].level_bits : 1;
     h->boxes_host.resize(nb);
     int deg = 10;
     for (int b = 0; b < nb; b++) {

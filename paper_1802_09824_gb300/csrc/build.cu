@@ -4,8 +4,17 @@
 // index (i N_side + j) N_side + k, particles are ordered by that index and,
 // inside a ground cell, by a Morton (or Peano-Hilbert, Sec. 4.1) key, so that
 // every octree node is one contiguous run of particles.  Leaves are the
-// largest octree cells holding at most leaf_max particles (the N_pp of
-// Sec. 3.1, the leaf size of Sec. 4.4).
+// largest cells holding at most leaf_max particles (the N_pp of Sec. 3.1, the
+// leaf size of Sec. 4.4); a level of the hierarchy is level_bits key bits:
+// 3 gives the octree cells, 1 splits every octree level into its three
+// binary sub-levels (half, quarter cell), which are key prefixes too.
+//
+// Leaf rule, evaluated independently for every particle k: k starts a leaf
+// iff k is the first particle of a ground cell, or the smallest cell that
+// holds both k-1 and k (their common key prefix) has more than leaf_max
+// particles -- then k-1 and k lie in different children of a cell that had
+// to be split.  Particles with identical keys (a finest cell) that number
+// more than leaf_max are cut into runs of leaf_max from the run's start.
 //
 // Positions are stored relative to a reference point of their leaf in FP32
 // (the FP64 wrap and the reference points are the only FP64 data on the
@@ -191,7 +200,7 @@ __global__ void k_cell_first(const uint64_t *keys, int64_t n, const BoxDev *boxe
 }
 
 // Leaf and group start flags (see the leaf rule in the file comment).
-__global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, int T, int leaf_max,
+__global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, int T, int leaf_max, int level_bits,
                         const int32_t *cell_first, int32_t *leaf_flag, int32_t *group_flag)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -227,7 +236,7 @@ __global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, in
                     lf = (hi - lo > leaf_max && ((k - lo) % leaf_max) == 0) ? 1 : 0;
                 } else {
                     const int hb = 63 - __clzll((long long)x);
-                    const int sh = 3 * (hb / 3 + 1);        // prefix shift of the common cell
+                    const int sh = level_bits * (hb / level_bits + 1);   // prefix shift of the common cell
                     const uint64_t P = Bk >> sh;
                     // is the common cell (holding k-1 and k) larger than leaf_max?
                     bool big;
@@ -259,65 +268,68 @@ __global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, in
     }
 }
 
-// Bounding box of each leaf (or group): FP64 reference point near the box
-// centre, FP32 half extents around it rounded up, FP32 reference point
-// relative to the ground cell's lower corner.
-__global__ void k_boxes(const int32_t *first, const int32_t *scan_total, int64_t n, const double *xw,
-                        const uint64_t *keys, const BoxDev *boxes, int T, double *ref, float4 *c4, float4 *h4,
-                        int32_t *cell_of, int32_t *box_of)
+// Orders doubles like their values when compared as signed 64-bit integers.
+__device__ __forceinline__ long long dkey(double x)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+__device__ __forceinline__ double dkey_inv(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
+// Bounding box of each leaf (or group), one thread per box: FP64 reference
+// point near the box centre, FP32 half extents around it rounded up, FP32
+// reference point relative to the ground cell's lower corner.
+//
+// The reference point is the centre rounded to a multiple of U = 2^(e-24),
+// the FP32 spacing of the box's largest |coordinate| (2^(e-1) <= m < 2^e),
+// so that an FP32 coordinate minus it is exact; rounding to a multiple of U
+// is done as (c + 1.5 2^52 U) - 1.5 2^52 U (round half to even).
+__global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const double *xw, const uint64_t *keys,
+                        const BoxDev *boxes, int T, double *ref, float4 *c4, float4 *h4, int32_t *cell_of,
+                        int32_t *box_of)
+{
     const int count = *scan_total;
-    for (int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < count; l += warps) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
         const int a = first[l], e = first[l + 1];
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int k = a + lane; k < e; k += 32) {
+        long long lo[3], hi[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) lo[d] = hi[d] = dkey(xw[3 * (int64_t)a + d]);
+        for (int k = a + 1; k < e; k++) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                double v = xw[3 * (int64_t)k + d];
-                lo[d] = fmin(lo[d], v);
-                hi[d] = fmax(hi[d], v);
+                const long long v = dkey(xw[3 * (int64_t)k + d]);
+                lo[d] = v < lo[d] ? v : lo[d];
+                hi[d] = v > hi[d] ? v : hi[d];
             }
         }
+        const uint64_t key = keys[a];
+        const int bi = 3 * T < 64 ? (int)(key >> (3 * T)) : 0;
+        const BoxDev &bx = boxes[bi];
+        const uint32_t ground = (uint32_t)((key >> (3 * bx.b)) & ((1ull << (3 * bx.g)) - 1ull));
+        const uint32_t gz = ground % bx.nside, gy = (ground / bx.nside) % bx.nside, gx = ground / (bx.nside * bx.nside);
+        const uint32_t gc[3] = {gx, gy, gz};
+        float c[3], hh[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-                hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-            }
+            const double vlo = dkey_inv(lo[d]), vhi = dkey_inv(hi[d]);
+            const double m = fmax(fabs(vlo), fabs(vhi));
+            const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1022;   // m = f 2^ex, f in [0.5, 1)
+            const double C = __longlong_as_double(((long long)(ex + 28 + 1023) << 52) | (1ll << 51));
+            const double cen = __dmul_rn(0.5, __dadd_rn(vlo, vhi));
+            const double r = __dsub_rn(__dadd_rn(cen, C), C);
+            const double half = fmax(__dsub_rn(vhi, r), __dsub_rn(r, vlo));
+            ref[3 * (int64_t)l + d] = r;
+            c[d] = __double2float_rn(__dsub_rn(r, __dmul_rn((double)gc[d], bx.h)));
+            hh[d] = __double2float_ru(half);
         }
-        if (lane == 0) {
-            const uint64_t key = keys[a];
-            const int bi = 3 * T < 64 ? (int)(key >> (3 * T)) : 0;
-            const BoxDev &bx = boxes[bi];
-            const uint32_t ground = (uint32_t)((key >> (3 * bx.b)) & ((1ull << (3 * bx.g)) - 1ull));
-            const uint32_t gz = ground % bx.nside, gy = (ground / bx.nside) % bx.nside,
-                           gx = ground / (bx.nside * bx.nside);
-            const double org[3] = {__dmul_rn((double)gx, bx.h), __dmul_rn((double)gy, bx.h),
-                                   __dmul_rn((double)gz, bx.h)};
-            float c[3], hh[3];
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                // reference point: the box centre snapped to a multiple of the
-                // FP32 spacing of the box's largest coordinate, so that the
-                // FP32 difference of any FP32 coordinate in it is exact
-                const double mx = fmax(fabs(lo[d]), fabs(hi[d]));
-                int ex;
-                frexp(mx, &ex);
-                const double cen = __dmul_rn(0.5, __dadd_rn(lo[d], hi[d]));
-                const double r = ldexp(rint(ldexp(cen, 24 - ex)), ex - 24);   // exact scalings
-                const double half = fmax(__dsub_rn(hi[d], r), __dsub_rn(r, lo[d]));
-                ref[3 * (int64_t)l + d] = r;
-                c[d] = __double2float_rn(__dsub_rn(r, org[d]));
-                hh[d] = __double2float_ru(half);
-            }
-            c4[l] = make_float4(c[0], c[1], c[2], 0.f);
-            h4[l] = make_float4(hh[0], hh[1], hh[2], 0.f);
-            if (cell_of) cell_of[l] = bx.cell_base + (int)ground;
-            if (box_of) box_of[l] = bi;
-        }
+        c4[l] = make_float4(c[0], c[1], c[2], 0.f);
+        h4[l] = make_float4(hh[0], hh[1], hh[2], 0.f);
+        if (cell_of) cell_of[l] = bx.cell_base + (int)ground;
+        if (box_of) box_of[l] = bi;
     }
 }
 
@@ -435,7 +447,8 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     k_cell_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(sk, n, boxes, nb, h->n_cells, T, cell_first);
     count_launch();
     if (n > 0)
-        k_flags<<<grid_for(n), kThreads, 0, s>>>(sk, n, boxes, T, h->max_leaf, cell_first, lflag, gflag);
+        k_flags<<<grid_for(n), kThreads, 0, s>>>(sk, n, boxes, T, h->max_leaf, h->level_bits, cell_first, lflag,
+                                                 gflag);
         count_launch();
     int rc = scan_exclusive_i32(lflag, lscan, n, nullptr, h->temp.p, s);
     if (rc) return rc;
@@ -451,12 +464,12 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
         cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
         cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
     }
-    const int box_grid = grid_for(n * 32 / 8 + 32);
-    k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
+    const int box_grid = grid_for(n);
+    k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
                                           static_cast<float4 *>(h->leaf_c4.p), static_cast<float4 *>(h->leaf_h4.p),
                                           nullptr, nullptr);
     count_launch();
-    k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, n, xw, sk, boxes, T,
+    k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, xw, sk, boxes, T,
                                           static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_c4.p),
                                           static_cast<float4 *>(h->group_h4.p), static_cast<int32_t *>(h->group_cell.p),
                                           static_cast<int32_t *>(h->group_box.p));

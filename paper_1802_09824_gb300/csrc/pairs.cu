@@ -34,6 +34,23 @@ struct PairArgs {
     uint32_t *status;
 };
 
+__device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// One warp per target group.  Lane t < 27 takes neighbour cell t (offset
+// (t/9-1, t/3%3-1, t%3-1)), skips it when the whole cell is beyond rcut of
+// the group's box, and contributes its leaf count; the warp then walks the
+// concatenated candidate leaves 32 at a time, each lane finding the
+// neighbour that owns its candidate by a binary search over the lanes'
+// exclusive prefix counts.  Candidates keep the order (neighbour, leaf), so
+// the list is deterministic.
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
 {
@@ -49,6 +66,27 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
         const float4 gc = a.group_c4[g], gh = a.group_h4[g];
         const float hc = (float)bx.h;
         const float rf2 = bx.rfilt2;
+        // this lane's neighbour cell
+        const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+        int l0 = 0, cnt = 0;
+        if (lane < 27) {
+            const int ax = gx + dx, ay = gy + dy, az = gz + dz;
+            const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
+            const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
+            const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+            const int nc = bx.cell_base + ((ax - sx * ns) * ns + (ay - sy * ns)) * ns + (az - sz * ns);
+            // the neighbour cell spans [d h, (d+1) h) in the group's cell frame
+            const float qx = fmaxf(fmaxf(dx * hc - (gc.x + gh.x), (gc.x - gh.x) - (dx + 1) * hc), 0.f);
+            const float qy = fmaxf(fmaxf(dy * hc - (gc.y + gh.y), (gc.y - gh.y) - (dy + 1) * hc), 0.f);
+            const float qz = fmaxf(fmaxf(dz * hc - (gc.z + gh.z), (gc.z - gh.z) - (dz + 1) * hc), 0.f);
+            if (qx * qx + qy * qy + qz * qz < rf2 * 1.0001f) {
+                l0 = a.cell_leaf_first[nc];
+                cnt = a.cell_leaf_first[nc + 1] - l0;
+            }
+        }
+        const int incl = warp_incl_scan_i(cnt, lane);
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
         double gref[3] = {0, 0, 0};
         int64_t base = 0;
         if (kFill) {
@@ -58,43 +96,49 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             base = a.off[g];
         }
         int64_t count = 0;
-        for (int nb = 0; nb < 27; nb++) {
-            const int dx = nb / 9 - 1, dy = (nb / 3) % 3 - 1, dz = nb % 3 - 1;
-            const int ax = gx + dx, ay = gy + dy, az = gz + dz;
-            const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
-            const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
-            const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
-            const int nc = bx.cell_base + ((ax - sx * ns) * ns + (ay - sy * ns)) * ns + (az - sz * ns);
-            const int l0 = a.cell_leaf_first[nc], l1 = a.cell_leaf_first[nc + 1];
-            const float ox = dx * hc, oy = dy * hc, oz = dz * hc;
-            for (int lb = l0; lb < l1; lb += 32) {
-                const int l = lb + lane;
-                bool acc = false;
-                if (l < l1) {
-                    const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
-                    float qx = fmaxf(fabsf((lc.x + ox) - gc.x) - (gh.x + lh.x), 0.f);
-                    float qy = fmaxf(fabsf((lc.y + oy) - gc.y) - (gh.y + lh.y), 0.f);
-                    float qz = fmaxf(fabsf((lc.z + oz) - gc.z) - (gh.z + lh.z), 0.f);
-                    acc = qx * qx + qy * qy + qz * qz < rf2;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                if (kFill && acc) {
-                    const int64_t pos = base + count + __popc(bal & lt);
-                    if (pos < a.cap) {
-                        const double *lr = a.leaf_ref + 3 * (int64_t)l;
-                        const double L = bx.L;
-                        float4 e;
-                        e.x = __double2float_rn((lr[0] + sx * L) - gref[0]);
-                        e.y = __double2float_rn((lr[1] + sy * L) - gref[1]);
-                        e.z = __double2float_rn((lr[2] + sz * L) - gref[2]);
-                        e.w = __int_as_float(l);
-                        a.ent[pos] = e;
-                    } else {
-                        atomicOr(a.status, ST_CAPACITY);
-                    }
-                }
-                count += __popc(bal);
+        for (int q0 = 0; q0 < total; q0 += 32) {
+            const int q = q0 + lane;
+            // owner: the largest lane o with excl_o <= q (counts are >= 0)
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, excl, o + step);
+                if (e <= q) o += step;
             }
+            const int lo0 = __shfl_sync(0xffffffffu, l0, o);
+            const int eo = __shfl_sync(0xffffffffu, excl, o);
+            bool acc = false;
+            int l = 0;
+            const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
+            if (q < total) {
+                l = lo0 + (q - eo);
+                const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
+                const float px = fmaxf(fabsf((lc.x + odx * hc) - gc.x) - (gh.x + lh.x), 0.f);
+                const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
+                const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
+                acc = px * px + py * py + pz * pz < rf2;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, acc);
+            if (kFill && acc) {
+                const int64_t pos = base + count + __popc(bal & lt);
+                if (pos < a.cap) {
+                    const int ax = gx + odx, ay = gy + ody, az = gz + odz;
+                    const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
+                    const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
+                    const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+                    const double *lr = a.leaf_ref + 3 * (int64_t)l;
+                    const double L = bx.L;
+                    float4 e;
+                    e.x = __double2float_rn((lr[0] + sx * L) - gref[0]);
+                    e.y = __double2float_rn((lr[1] + sy * L) - gref[1]);
+                    e.z = __double2float_rn((lr[2] + sz * L) - gref[2]);
+                    e.w = __int_as_float(l);
+                    a.ent[pos] = e;
+                } else {
+                    atomicOr(a.status, ST_CAPACITY);
+                }
+            }
+            count += __popc(bal);
         }
         if (!kFill && lane == 0) a.cnt[g] = count;
     }

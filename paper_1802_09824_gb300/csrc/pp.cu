@@ -3,11 +3,13 @@
 // One warp takes one target group at a time from a global queue (the task
 // queue of Sec. 4.3, ground cells rolled in ascending order) and holds one
 // target particle per lane in registers.  The source leaves of the group's
-// list are streamed through shared memory: lanes load a leaf's particles with
-// coalesced float4 loads, shift them into the group frame (one FP32 add of
-// the pair's offset), drop those farther than R_cut from the group's bounding
-// box, and append the rest to a per-warp buffer; a full buffer is summed with
-// every lane reading the same source (shared-memory broadcast).
+// list are streamed through shared memory: lanes load the leaves' particles
+// with float4 loads (32 useful loads per round whatever the leaf sizes),
+// shift them into the group frame (one FP32 add of the pair's offset), drop
+// those farther than R_cut from the group's bounding box, and append the rest
+// to a per-warp buffer as pairs; a full buffer is summed with every lane
+// reading the same two sources (shared-memory broadcast) and evaluating both
+// with packed FP32x2 instructions.
 //
 // Per pair (Eq. (split), Plummer factor, hard cutoff):
 //   r2 = |d|^2,  w = m_j f(r) / (r2 + eps^2)^{3/2}  if r2 < rcut^2 else 0
@@ -19,9 +21,13 @@
 namespace phpp {
 namespace {
 
+#ifndef PHPP_PP_MIN_BLOCKS
+#define PHPP_PP_MIN_BLOCKS 2   // resident 8-warp blocks per SM the register budget must allow
+#endif
+
 constexpr int kPPWarps = 8;
 constexpr int kPPThreads = kPPWarps * 32;
-constexpr int kJBuf = 256;
+constexpr int kJBuf = 256;      // staged sources per warp (even)
 
 __device__ __forceinline__ float rsqrt_sfu(float x)
 {
@@ -74,63 +80,142 @@ struct Kahan3 {
     }
 };
 
-// One pair: accumulate m_j f(r) d / (r^2 + eps^2)^{3/2} into (px, py, pz).
-template <int NPOLY>
-__device__ __forceinline__ void interact(const float4 pj, const float4 xi, const float *poly, float eps2, float rcut2,
-                                         float c_v, float c_e, float &px, float &py, float &pz)
+// ---- packed FP32 pairs (f32x2, sm_100+): two sources per instruction
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pk(float lo, float hi)
 {
-    const float dx = pj.x - xi.x, dy = pj.y - xi.y, dz = pj.z - xi.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f2_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float hi_of(f2_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
+{
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Constants of one box, each duplicated into both halves of a pair.
+template <int NPOLY>
+struct PairConsts {
+    f2_t poly[NPOLY + 1];
+    f2_t eps2, c_v, c_e, m15, c15, m1;
+    float rcut2;
+};
+
+// Two sources (A = x0 x1 y0 y1, B = z0 z1 m0 m1) against one target: add
+// m_j f(r) d / (r^2 + eps^2)^{3/2} into the pair accumulators.
+template <int NPOLY>
+__device__ __forceinline__ void interact2(const float4 a, const float4 b, const f2_t xi, const f2_t yi, const f2_t zi,
+                                          const PairConsts<NPOLY> &c, f2_t &px, f2_t &py, f2_t &pz)
+{
+    const f2_t dx = sub2(pk(a.x, a.y), xi), dy = sub2(pk(a.z, a.w), yi), dz = sub2(pk(b.x, b.y), zi);
+    f2_t r2 = mul2(dx, dx);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
     // (r2 + eps2)^(-3/2): SFU rsqrt y, then the first-order Newton
     // correction y^3 (1 + 3/2 (1 - x y^2)), which removes the SFU error
-    const float x = r2 + eps2;
-    const float y = rsqrt_sfu(x);
-    const float y2 = y * y;
-    const float y3 = y2 * y;
-    const float e15 = fmaf(x * -1.5f, y2, 1.5f);
-    const float inv3 = fmaf(y3, e15, y3);
-    const float t = sqrt_sfu(r2 * c_v) - 1.f;
-    float hp = poly[NPOLY];
+    const f2_t x = add2(r2, c.eps2);
+    const f2_t y = pk(rsqrt_sfu(lo_of(x)), rsqrt_sfu(hi_of(x)));
+    const f2_t y2 = mul2(y, y);
+    const f2_t y3 = mul2(y2, y);
+    const f2_t e15 = fma2(mul2(x, c.m15), y2, c.c15);
+    const f2_t inv3 = fma2(y3, e15, y3);
+    const f2_t sv = mul2(r2, c.c_v);
+    const f2_t t = add2(pk(sqrt_sfu(lo_of(sv)), sqrt_sfu(hi_of(sv))), c.m1);
+    f2_t h = c.poly[NPOLY];
 #pragma unroll
-    for (int q = NPOLY - 1; q >= 0; q--) hp = fmaf(hp, t, poly[q]);
-    const float f = ex2_sfu(r2 * c_e) * hp;
-    float w = (pj.w * f) * inv3;
-    w = r2 < rcut2 ? w : 0.f;
-    px = fmaf(w, dx, px);
-    py = fmaf(w, dy, py);
-    pz = fmaf(w, dz, pz);
+    for (int q = NPOLY - 1; q >= 0; q--) h = fma2(h, t, c.poly[q]);
+    const f2_t ea = mul2(r2, c.c_e);
+    const f2_t f = mul2(pk(ex2_sfu(lo_of(ea)), ex2_sfu(hi_of(ea))), h);
+    const f2_t w = mul2(mul2(pk(b.z, b.w), f), inv3);
+    const float w0 = lo_of(r2) < c.rcut2 ? lo_of(w) : 0.f;
+    const float w1 = hi_of(r2) < c.rcut2 ? hi_of(w) : 0.f;
+    const f2_t wm = pk(w0, w1);
+    px = fma2(wm, dx, px);
+    py = fma2(wm, dy, py);
+    pz = fma2(wm, dz, pz);
 }
 
-// Sum a staged buffer: plain FP32 partial sums over runs of kChunk sources,
-// each run added to the total with Kahan compensation.
-constexpr int kChunk = 16;
+// Sum a staged buffer of npair source pairs: plain FP32 partial sums over
+// runs of kRun pairs (16 sources), each run added to the target's total
+// with Kahan compensation.
+constexpr int kRun = 8;
 
 template <int NPOLY>
-__device__ __forceinline__ void sum_buffer(const float4 *buf, int nbuf, const float4 xi, const float *poly,
-                                           float eps2, float rcut2, float c_v, float c_e, Kahan3 &k)
+__device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int npair, const f2_t xi, const f2_t yi,
+                                           const f2_t zi, const PairConsts<NPOLY> &c, Kahan3 &k)
 {
-    int jj = 0;
-    for (; jj + kChunk <= nbuf; jj += kChunk) {
-        float px = 0.f, py = 0.f, pz = 0.f;
+    int m = 0;
+    for (; m + kRun <= npair; m += kRun) {
+        f2_t px = 0ull, py = 0ull, pz = 0ull;
 #pragma unroll 4
-        for (int u = 0; u < kChunk; u++)
-            interact<NPOLY>(buf[jj + u], xi, poly, eps2, rcut2, c_v, c_e, px, py, pz);
-        k.add(px, py, pz);
+        for (int u = 0; u < kRun; u++) interact2<NPOLY>(A[m + u], B[m + u], xi, yi, zi, c, px, py, pz);
+        k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
     }
-    if (jj < nbuf) {
-        float px = 0.f, py = 0.f, pz = 0.f;
-        for (; jj < nbuf; jj++) interact<NPOLY>(buf[jj], xi, poly, eps2, rcut2, c_v, c_e, px, py, pz);
-        k.add(px, py, pz);
+    if (m < npair) {
+        f2_t px = 0ull, py = 0ull, pz = 0ull;
+        for (; m < npair; m++) interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
+        k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
     }
 }
 
-template <int NPOLY>
-__global__ void __launch_bounds__(kPPThreads, 4) k_pp_exact(PPArgs a)
+__device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 {
-    __shared__ float4 sbuf[kPPWarps][kJBuf];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Source staging and summation for one target group.  Entries are taken 32
+// at a time, one per lane; the lanes' leaf sizes are prefix-summed and the
+// concatenated source particles are loaded 32 per round, each lane finding
+// the entry of its particle by a binary search over the prefix sums, so that
+// every lane loads a useful particle whatever the leaf sizes.  Kept sources
+// are written as pairs into the warp's buffer; a full buffer is summed.
+template <int NPOLY>
+__global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp_exact(PPArgs a)
+{
+    __shared__ float4 sA[kPPWarps][kJBuf / 2];
+    __shared__ float4 sB[kPPWarps][kJBuf / 2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    float4 *buf = sbuf[w];
+    float4 *A = sA[w], *Bq = sB[w];
+    float *Af = reinterpret_cast<float *>(A), *Bf = reinterpret_cast<float *>(Bq);
     const int ng = *a.n_groups;
     unsigned long long inter = 0, staged = 0;
     for (;;) {
@@ -140,49 +225,95 @@ __global__ void __launch_bounds__(kPPThreads, 4) k_pp_exact(PPArgs a)
         if (g >= ng) break;
         const int i0 = a.group_first[g], ni = a.group_first[g + 1] - i0;
         const BoxDev &bx = a.boxes[a.group_box[g]];
-        float poly[NPOLY + 1];
+        PairConsts<NPOLY> c;
 #pragma unroll
-        for (int q = 0; q <= NPOLY; q++) poly[q] = bx.poly[q];
-        const float eps2 = bx.eps2, rcut2 = bx.rcut2, c_v = bx.c_v, c_e = bx.c_e, rf2 = bx.rfilt2;
+        for (int q = 0; q <= NPOLY; q++) c.poly[q] = pk(bx.poly[q], bx.poly[q]);
+        c.eps2 = pk(bx.eps2, bx.eps2);
+        c.c_v = pk(bx.c_v, bx.c_v);
+        c.c_e = pk(bx.c_e, bx.c_e);
+        c.m15 = pk(-1.5f, -1.5f);
+        c.c15 = pk(1.5f, 1.5f);
+        c.m1 = pk(-1.f, -1.f);
+        c.rcut2 = bx.rcut2;
+        const float rf2 = bx.rfilt2;
         const float4 gh = a.group_h4[g];
-        const float4 xi = lane < ni ? a.pos_group[i0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 xi4 = lane < ni ? a.pos_group[i0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const f2_t xi = pk(xi4.x, xi4.x), yi = pk(xi4.y, xi4.y), zi = pk(xi4.z, xi4.z);
         Kahan3 k;
         int nbuf = 0;
         const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
-        for (int64_t e = a.group_off[g]; e < e1; e++) {
-            const float4 ent = a.entries[e];
-            const int leaf = __float_as_int(ent.w);
-            const int j1 = a.leaf_first[leaf + 1];
-            for (int jb = a.leaf_first[leaf]; jb < j1; jb += 32) {
-                const int j = jb + lane;
+        for (int64_t eb = a.group_off[g]; eb < e1; eb += 32) {
+            const int64_t e = eb + lane;
+            float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+            int l0 = 0, cnt = 0;
+            if (e < e1) {
+                ent = a.entries[e];
+                const int leaf = __float_as_int(ent.w);
+                l0 = a.leaf_first[leaf];
+                cnt = a.leaf_first[leaf + 1] - l0;
+            }
+            const int incl = warp_incl_scan_i(cnt, lane);
+            const int excl = incl - cnt;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, o + step);
+                    if (ex <= q) o += step;
+                }
+                const int j = __shfl_sync(0xffffffffu, l0, o) + (q - __shfl_sync(0xffffffffu, excl, o));
+                const float ox = __shfl_sync(0xffffffffu, ent.x, o);
+                const float oy = __shfl_sync(0xffffffffu, ent.y, o);
+                const float oz = __shfl_sync(0xffffffffu, ent.z, o);
                 float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
                 bool keep = false;
-                if (j < j1) {
+                if (q < total) {
                     p = a.pos_leaf[j];
-                    p.x = __fadd_rn(p.x, ent.x);
-                    p.y = __fadd_rn(p.y, ent.y);
-                    p.z = __fadd_rn(p.z, ent.z);
+                    p.x = __fadd_rn(p.x, ox);
+                    p.y = __fadd_rn(p.y, oy);
+                    p.z = __fadd_rn(p.z, oz);
                     const float qx = fmaxf(fabsf(p.x) - gh.x, 0.f);
                     const float qy = fmaxf(fabsf(p.y) - gh.y, 0.f);
                     const float qz = fmaxf(fabsf(p.z) - gh.z, 0.f);
                     keep = qx * qx + qy * qy + qz * qz < rf2;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                const int cnt = __popc(bal);
-                if (nbuf + cnt > kJBuf) {
+                const int nk = __popc(bal);
+                if (nbuf + nk > kJBuf) {
+                    if (nbuf & 1) {   // pad to a whole pair with a massless source
+                        if (lane == 0) {
+                            Af[(nbuf >> 1) * 4 + 1] = 0.f; Af[(nbuf >> 1) * 4 + 3] = 0.f;
+                            Bf[(nbuf >> 1) * 4 + 1] = 0.f; Bf[(nbuf >> 1) * 4 + 3] = 0.f;
+                        }
+                    }
                     __syncwarp();
-                    sum_buffer<NPOLY>(buf, nbuf, xi, poly, eps2, rcut2, c_v, c_e, k);
+                    sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
                     inter += (unsigned long long)nbuf * ni;
                     staged += nbuf;
                     nbuf = 0;
                     __syncwarp();
                 }
-                if (keep) buf[nbuf + __popc(bal & lt)] = p;
-                nbuf += cnt;
+                if (keep) {
+                    const int idx = nbuf + __popc(bal & lt);
+                    const int m = idx >> 1, sl = idx & 1;
+                    Af[m * 4 + sl] = p.x;
+                    Af[m * 4 + 2 + sl] = p.y;
+                    Bf[m * 4 + sl] = p.z;
+                    Bf[m * 4 + 2 + sl] = p.w;
+                }
+                nbuf += nk;
+            }
+        }
+        if (nbuf & 1) {
+            if (lane == 0) {
+                Af[(nbuf >> 1) * 4 + 1] = 0.f; Af[(nbuf >> 1) * 4 + 3] = 0.f;
+                Bf[(nbuf >> 1) * 4 + 1] = 0.f; Bf[(nbuf >> 1) * 4 + 3] = 0.f;
             }
         }
         __syncwarp();
-        sum_buffer<NPOLY>(buf, nbuf, xi, poly, eps2, rcut2, c_v, c_e, k);
+        sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
         inter += (unsigned long long)nbuf * ni;
         staged += nbuf;
         __syncwarp();

@@ -42,12 +42,12 @@ def check_parity(got, ref_res, G=1.0, p99=P99_TOL, emax=MAX_TOL):
     return q, m
 
 
-def gpu_accel(B, ps, key_kind=0, leaf_max=None, pos_dtype=np.float32, host=False, group_size=0):
+def gpu_accel(B, ps, key_kind=0, leaf_max=None, pos_dtype=np.float32, host=False, group_size=0, level_bits=0):
     """Accelerations of a ParticleSet through the C ABI (batched if B > 1)."""
     import torch
     pos = ps.pos.astype(pos_dtype)
-    prms = [B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max or bp.leaf_max, key_kind, group_size)
-            for bp in ps.boxes]
+    prms = [B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max or bp.leaf_max, key_kind, group_size,
+                          level_bits) for bp in ps.boxes]
     if host:
         tpos = torch.from_numpy(np.ascontiguousarray(pos))
         tmass = torch.from_numpy(ps.mass)

@@ -31,23 +31,24 @@ def _snapped(centre, half):
     return ref, np.maximum(hi - ref, ref - lo)
 
 
-def _build(B, ps, kind=0, leaf_max=16):
+def _build(B, ps, kind=0, leaf_max=16, level_bits=1):
     import torch
     bp = ps.boxes[0]
-    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max, kind)
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max, kind, 0, level_bits)
     lv = B.ph_build_leaves(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm)
     torch.cuda.synchronize()
     return lv, B.ph_leaves_get_view(lv)
 
 
+@pytest.mark.parametrize("level_bits", [1, 3])
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("clustered", [False, True])
 @pytest.mark.parametrize("n", [1, 2, 33, 3000, 20000])
-def test_keys_sort_leaves_groups_bit_exact(gpu_lib, kind, clustered, n):
+def test_keys_sort_leaves_groups_bit_exact(gpu_lib, kind, clustered, n, level_bits):
     B = gpu_lib
     ps = _set(n=n, clustered=clustered)
-    lv, v = _build(B, ps, kind)
-    t = T.BoxTree(ps.pos, 1.0, ps.boxes[0].rcut, 16, 32, kind, T=v["key_bits"])
+    lv, v = _build(B, ps, kind, level_bits=level_bits)
+    t = T.BoxTree(ps.pos, 1.0, ps.boxes[0].rcut, 16, 32, kind, T=v["key_bits"], level_bits=level_bits)
     assert v["n_leaves"] == len(t.leaf_first) - 1
     assert v["n_groups"] == len(t.group_first) - 1
     np.testing.assert_array_equal(v["keys"].cpu().numpy().astype(np.uint64), t.keys)
@@ -79,25 +80,27 @@ def test_coincident_particles_chunk(gpu_lib):
     p = np.tile(np.array([[0.1, 0.2, 0.3]], np.float32), (70, 1))
     bp = synth.BoxParams(L=1.0, G=1.0, eps=1e-3, rs=1.25 / 32, rcut=4.5 * 1.25 / 32, leaf_max=32)
     ps = synth._single(p, np.full(70, 1 / 70, np.float32), bp, "c")
-    lv, v = _build(gpu_lib, ps, 0, leaf_max=32)
-    assert v["leaf_first"].cpu().numpy().tolist() == [0, 32, 64, 70]
-    gpu_lib.ph_free(lv)
+    for lb in (1, 3):
+        lv, v = _build(gpu_lib, ps, 0, leaf_max=32, level_bits=lb)
+        assert v["leaf_first"].cpu().numpy().tolist() == [0, 32, 64, 70]
+        gpu_lib.ph_free(lv)
 
 
+@pytest.mark.parametrize("level_bits", [1, 3])
 @pytest.mark.parametrize("clustered", [False, True])
 @pytest.mark.parametrize("L,rcut", [(1.0, 0.17578125), (1.0, 0.3)])
-def test_pair_list_matches_box_relation(gpu_lib, clustered, L, rcut):
+def test_pair_list_matches_box_relation(gpu_lib, clustered, L, rcut, level_bits):
     import torch
     B = gpu_lib
     ps = _set(n=4000, clustered=clustered, L=L)
     bp = ps.boxes[0]
-    prm = B.make_params(L, 1.0, bp.eps, rcut / 4.5, rcut, 16)
+    prm = B.make_params(L, 1.0, bp.eps, rcut / 4.5, rcut, 16, 0, 0, level_bits)
     lv = B.ph_build_leaves(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm)
     pr = B.ph_leaf_pairs(lv)
     torch.cuda.synchronize()
     v = B.ph_leaves_get_view(lv)
     pv = B.ph_pairs_get_view(pr)
-    t = T.BoxTree(ps.pos, L, rcut, 16, 32, 0, T=v["key_bits"])
+    t = T.BoxTree(ps.pos, L, rcut, 16, 32, 0, T=v["key_bits"], level_bits=level_bits)
     lc, _ = _snapped(*t.leaf_boxes())
     gc, _ = _snapped(*t.group_boxes())
     off = pv["group_off"].cpu().numpy()

@@ -20,10 +20,11 @@ def test_uniform_4096_full(gpu_lib, kind):
     gpu_lib.ph_free(lv)
 
 
+@pytest.mark.parametrize("level_bits", [1, 3])
 @pytest.mark.parametrize("leaf_max", [1, 8, 64, 256])
-def test_leaf_size_does_not_change_result(gpu_lib, leaf_max):
+def test_leaf_size_does_not_change_result(gpu_lib, leaf_max, level_bits):
     ps = synth.workload("uniform_small", scale=3000)
-    got, lv, pr = gpu_accel(gpu_lib, ps, leaf_max=leaf_max)
+    got, lv, pr = gpu_accel(gpu_lib, ps, leaf_max=leaf_max, level_bits=level_bits)
     check_parity(got, oracle_accel(ps))
     gpu_lib.ph_free(pr)
     gpu_lib.ph_free(lv)
@@ -155,13 +156,13 @@ def test_count_within_matches_oracle(gpu_lib):
     B = gpu_lib
     for ps in (synth.workload("uniform_small"), synth.workload("nfw_mix_256", scale=24)):
         got, lv, pr = gpu_accel(B, ps)
+        ev, st = B.ph_pp_counters(pr)
         n = B.ph_count_within(lv, pr)
         ref = oracle_accel(ps, box=0)
         exp = int(ref.n_within.sum())
         # pairs within FP32 rounding of rcut may be counted either way
         near = int(np.sum(ref.near_abs > 0))
         assert abs(n - exp) <= near, (n, exp, near)
-        ev, st = B.ph_pp_counters(pr)
         assert ev >= n + ps.n and st > 0
         B.ph_free(pr)
         B.ph_free(lv)

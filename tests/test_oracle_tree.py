@@ -73,19 +73,20 @@ def test_keys_box_prefix_orders_boxes():
 
 
 # ------------------------------------------------------------------ tree
-def _tree(n=3000, seed=2, leaf_max=16, group=32, kind=0, clustered=False):
+def _tree(n=3000, seed=2, leaf_max=16, group=32, kind=0, clustered=False, level_bits=1):
     rng = np.random.default_rng(seed)
     p = rng.random((n, 3))
     if clustered:
         p[: n // 2] = 0.3 + 0.01 * rng.standard_normal((n // 2, 3))
         p = np.mod(p, 1.0)
-    return p, T.BoxTree(p, 1.0, 0.17578125, leaf_max, group, kind)
+    return p, T.BoxTree(p, 1.0, 0.17578125, leaf_max, group, kind, level_bits=level_bits)
 
 
+@pytest.mark.parametrize("level_bits", [1, 3])
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("clustered", [False, True])
-def test_leaves_are_maximal_octree_cells(kind, clustered):
-    p, t = _tree(kind=kind, clustered=clustered)
+def test_leaves_are_maximal_cells(kind, clustered, level_bits):
+    p, t = _tree(kind=kind, clustered=clustered, level_bits=level_bits)
     lf = t.leaf_first
     cnt = np.diff(lf)
     assert lf[0] == 0 and lf[-1] == len(p) and np.all(cnt >= 1)
@@ -97,8 +98,9 @@ def test_leaves_are_maximal_octree_cells(kind, clustered):
         # particle: the first cell holding <= leaf_max particles must be
         # exactly this leaf (a maximal octree cell under the count rule)
         k0 = int(keys[a])
-        for lvl in range(b + 1):
-            shift = 3 * (b - lvl)
+        s = level_bits
+        for lvl in range(3 * b // s + 1):
+            shift = 3 * b - s * lvl
             pre = k0 >> shift
             lo = int(np.searchsorted(keys, np.uint64(pre << shift)))
             hi = int(np.searchsorted(keys, np.uint64((pre + 1) << shift))) if pre + 1 < (1 << (64 - shift)) else len(keys)
@@ -110,10 +112,19 @@ def test_leaves_are_maximal_octree_cells(kind, clustered):
             assert e - a <= t.leaf_max
 
 
-def test_coincident_keys_are_chunked():
+@pytest.mark.parametrize("level_bits", [1, 3])
+def test_coincident_keys_are_chunked(level_bits):
     p = np.tile(np.array([[0.1, 0.2, 0.3]]), (70, 1))
-    t = T.BoxTree(p, 1.0, 0.17578125, 32, 32)
+    t = T.BoxTree(p, 1.0, 0.17578125, 32, 32, level_bits=level_bits)
     assert np.diff(t.leaf_first).tolist() == [32, 32, 6]
+
+
+def test_binary_levels_give_fuller_leaves():
+    # a uniform cell of 512 particles: octree leaves hold ~8, binary-level
+    # leaves ~16-32 (the cells halve instead of dividing by 8)
+    _, t3 = _tree(n=32768, leaf_max=32, level_bits=3)
+    _, t1 = _tree(n=32768, leaf_max=32, level_bits=1)
+    assert np.diff(t1.leaf_first).mean() > 1.8 * np.diff(t3.leaf_first).mean()
 
 
 def test_groups_stay_inside_ground_cells():
