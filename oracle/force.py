@@ -32,6 +32,11 @@ def _load():
         lib.phor_split_factor.restype = ctypes.c_double
         lib.phor_split_factor_v.argtypes = [ctypes.c_int64, dp, ctypes.c_double, dp]
         lib.phor_split_factor_v.restype = None
+        lib.phor_mlp_factor.argtypes = [dp, ctypes.c_double, ctypes.c_double]
+        lib.phor_mlp_factor.restype = ctypes.c_double
+        lib.phor_accel_mlp.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, dp, ctypes.c_int64, i64p, dp]
+        lib.phor_accel_mlp.restype = None
         lib.phor_num_threads.argtypes = []
         lib.phor_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -99,3 +104,29 @@ def accel(pos, mass, L, G, eps, rs, rcut, targets=None, near_tol=1e-5) -> AccelR
                        float(rcut), nt, tp, _dp(acc), _dp(abs_sum), _ip(n_within),
                        _dp(near_abs), float(near_tol))
     return AccelResult(acc, abs_sum, n_within, near_abs)
+
+
+def mlp_factor(weights, r, rcut):
+    """The network's factor at separations r (C oracle, double)."""
+    lib = _load()
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    return np.array([lib.phor_mlp_factor(_dp(w), float(x), float(rcut)) for x in np.atleast_1d(r)])
+
+
+def accel_mlp(pos, mass, L, G, eps, rcut, weights, targets=None):
+    """Accelerations with the network in place of Eq. (split)."""
+    lib = _load()
+    pos = np.ascontiguousarray(np.asarray(pos, np.float64))
+    mass = np.ascontiguousarray(np.asarray(mass, np.float64))
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    n = pos.shape[0]
+    if targets is None:
+        nt, tp = n, None
+    else:
+        targets = np.ascontiguousarray(np.asarray(targets, np.int64))
+        nt, tp = targets.size, _ip(targets)
+    acc = np.zeros((nt, 3))
+    if n and nt:
+        lib.phor_accel_mlp(n, _dp(pos), _dp(mass), float(L), float(G), float(eps), float(rcut), _dp(w), nt, tp,
+                           _dp(acc))
+    return acc

@@ -103,6 +103,55 @@ void phor_accel(int64_t n, const double *pos, const double *mass,
     }
 }
 
+/*
+ * The learned factor: the 1-16-16-1 SiLU network evaluated in double at
+ * z0 = 2 r / rcut - 1.  w[321] = W1[16], b1[16], W2[16][16] (row k = weights
+ * into unit k), b2[16], W3[16], b3.
+ */
+static double silu(double a) { return a / (1.0 + exp(-a)); }
+
+double phor_mlp_factor(const double *w, double r, double rcut)
+{
+    const double *W1 = w, *b1 = w + 16, *W2 = w + 32, *b2 = w + 288, *W3 = w + 304, b3 = w[320];
+    double z0 = 2.0 * r / rcut - 1.0, h1[16], y = b3;
+    for (int j = 0; j < 16; j++) h1[j] = silu(W1[j] * z0 + b1[j]);
+    for (int k = 0; k < 16; k++) {
+        double a = b2[k];
+        for (int j = 0; j < 16; j++) a += W2[16 * k + j] * h1[j];
+        y += W3[k] * silu(a);
+    }
+    return y;
+}
+
+/* Same sum as phor_accel with the network standing in for Eq. (split). */
+void phor_accel_mlp(int64_t n, const double *pos, const double *mass, double L, double G, double eps,
+                    double rcut, const double *w, int64_t nt, const int64_t *targets, double *acc)
+{
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t t = 0; t < nt; t++) {
+        const int64_t i = targets ? targets[t] : t;
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = min_image(pos[3 * j] - pos[3 * i], L);
+            double dy = min_image(pos[3 * j + 1] - pos[3 * i + 1], L);
+            double dz = min_image(pos[3 * j + 2] - pos[3 * i + 2], L);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            if (!(r < rcut)) continue;
+            double re2 = r2 + eps2;
+            double wgt = G * mass[j] * phor_mlp_factor(w, r, rcut) / (re2 * sqrt(re2));
+            ax += wgt * dx;
+            ay += wgt * dy;
+            az += wgt * dz;
+        }
+        acc[3 * t] = ax;
+        acc[3 * t + 1] = ay;
+        acc[3 * t + 2] = az;
+    }
+}
+
 /* Number of threads OpenMP will use for the parallel loop above. */
 int phor_num_threads(void)
 {
