@@ -228,6 +228,52 @@ int ph_pp_counters(const ph_pairs *pairs, int64_t *interactions, int64_t *staged
  * coincident particles).  Synchronises. */
 int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_within, void *stream);
 
+/* ------------------------------------------------------------ learned factor
+ * A 1-16-16-1 network with SiLU activations stands in for Eq. (split) in the
+ * PP inner loop (PH_G_LEARNED).  Input z0 = 2 r / rcut - 1; output g_hat(r).
+ * Parameters, flat float32[321]: W1[16], b1[16], W2[16][16] (row k holds the
+ * weights into unit k), b2[16], W3[16], b3.  Inference in the PP kernel:
+ * layer 1 and the SiLUs in FP32 (SFU ex2/rcp), layer 2 as BF16 tensor-core
+ * MMAs (mma.sync m16n8k16, FP32 accumulation, activations and weights split
+ * into BF16 hi + lo parts).  A handle records the largest relative error of
+ * g_hat against the exact factor over r in [0, rcut) (the exact path judges
+ * the network); ph_pp_accel falls back to the exact factor and returns
+ * PH_WARN_FALLBACK when that error is above the handle's tolerance or the
+ * box's rcut / rs differs from the one the network was trained for.
+ */
+#define PH_MLP_PARAMS 321
+
+typedef struct ph_train_params {
+    int64_t  n_samples;   /* training samples r ~ U[0, rcut) (e.g. 10^6)           */
+    int32_t  batch;       /* samples per Adam step                                  */
+    int32_t  steps;       /* Adam steps                                             */
+    float    lr0, lr_min; /* cosine learning-rate schedule from lr0 to lr_min       */
+    float    tol;         /* accepted largest relative error of g_hat (0 = 1e-3)    */
+    int32_t  reserved;
+    uint64_t seed;        /* init stream = seed, samples = seed+1, batches = seed+2 */
+} ph_train_params;
+
+/*
+ * Train the network on the GPU (the project's own forward, backward and Adam
+ * kernels, FP32): samples and their exact-factor targets are generated on the
+ * device; loss = mean ((g_hat - g) / g)^2 over each batch.  init_weights:
+ * host float[321], or NULL for the seeded initialisation.  Synchronises.
+ */
+int ph_mlp_train(const ph_train_params *tp, double rs, double rcut, const float *init_weights,
+                 void *stream, ph_mlp **mlp);
+
+/* A handle from given weights (host or device float[321]); validates them. */
+int ph_mlp_create(const float *weights, double rs, double rcut, float tol, void *stream, ph_mlp **mlp);
+
+/* Weights (host float[321], nullable), validated error and last training loss. */
+int ph_mlp_get(const ph_mlp *mlp, float *weights, float *max_rel_err, float *last_loss);
+
+/* One forward + backward pass of the training kernel on given inputs
+ * (host or device float[n] each): gradient of the mean relative squared
+ * error (host float[321]) and the loss.  Synchronises. */
+int ph_mlp_loss_grad(const float *weights, const float *z0, const float *target, int64_t n, float *grad,
+                     float *loss, void *stream);
+
 /* ------------------------------------------------------------ no allocation
  * ph_accel_noalloc -- the whole step (ph_accel with the exact factor) for
  * one small box, without allocating anything.

@@ -55,6 +55,15 @@ class ph_leaves_view(ctypes.Structure):
                 ("g", ctypes.c_int32 * 4), ("key_bits", ctypes.c_int32), ("group_size", ctypes.c_int32)]
 
 
+class ph_train_params(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("batch", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("lr0", ctypes.c_float), ("lr_min", ctypes.c_float), ("tol", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+PH_MLP_PARAMS = 321
+
+
 class ph_pairs_view(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p)]
@@ -82,6 +91,12 @@ _SIGS = {
     "ph_count_within": ([_VP, _VP, ctypes.POINTER(ctypes.c_int64), _VP], ctypes.c_int),
     "ph_launch_counter": ([], ctypes.c_int64),
     "ph_accel_noalloc": ([_VP, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), _VP, _VP], ctypes.c_int),
+    "ph_mlp_train": ([ctypes.POINTER(ph_train_params), ctypes.c_double, ctypes.c_double, _VP, _VP,
+                      ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_mlp_create": ([_VP, ctypes.c_double, ctypes.c_double, ctypes.c_float, _VP, ctypes.POINTER(_VP)],
+                      ctypes.c_int),
+    "ph_mlp_get": ([_VP, _VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "ph_mlp_loss_grad": ([_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_float), _VP], ctypes.c_int),
 }
 
 
@@ -257,6 +272,48 @@ def ph_accel_noalloc(pos, mass, params, acc, stream=None):
     fixed scratch array (no device allocation); device tensors only."""
     return _check(lib().ph_accel_noalloc(_ptr(pos), _ptr(mass), int(pos.shape[0]), ctypes.byref(params),
                                          _ptr(acc), _stream(stream)))
+
+
+def make_train_params(n_samples=1_000_000, batch=4096, steps=40_000, lr0=1e-2, lr_min=1e-5, tol=1e-3, seed=12345):
+    return ph_train_params(int(n_samples), int(batch), int(steps), float(lr0), float(lr_min), float(tol), 0,
+                           int(seed))
+
+
+def ph_mlp_train(tp, rs, rcut, init_weights=None, stream=None):
+    """Train the 1-16-16-1 network on the GPU; returns the handle."""
+    out = ctypes.c_void_p(None)
+    w = None if init_weights is None else np.ascontiguousarray(np.asarray(init_weights, np.float32))
+    _check(lib().ph_mlp_train(ctypes.byref(tp), float(rs), float(rcut), _ptr(w), _stream(stream),
+                              ctypes.byref(out)))
+    return Handle(out.value)
+
+
+def ph_mlp_create(weights, rs, rcut, tol=0.0, stream=None):
+    out = ctypes.c_void_p(None)
+    w = np.ascontiguousarray(np.asarray(weights, np.float32))
+    _check(lib().ph_mlp_create(_ptr(w), float(rs), float(rcut), float(tol), _stream(stream), ctypes.byref(out)))
+    return Handle(out.value)
+
+
+def ph_mlp_get(mlp):
+    """(weights float32[321], validated max relative error, last loss)."""
+    w = np.zeros(PH_MLP_PARAMS, np.float32)
+    e = ctypes.c_float(0)
+    l = ctypes.c_float(0)
+    _check(lib().ph_mlp_get(mlp.ptr, _ptr(w), ctypes.byref(e), ctypes.byref(l)))
+    return w, e.value, l.value
+
+
+def ph_mlp_loss_grad(weights, z0, target, stream=None):
+    """Gradient (float32[321]) and loss of one forward/backward pass."""
+    w = np.ascontiguousarray(np.asarray(weights, np.float32))
+    z = np.ascontiguousarray(np.asarray(z0, np.float32))
+    t = np.ascontiguousarray(np.asarray(target, np.float32))
+    g = np.zeros(PH_MLP_PARAMS, np.float32)
+    loss = ctypes.c_float(0)
+    _check(lib().ph_mlp_loss_grad(_ptr(w), _ptr(z), _ptr(t), int(z.size), _ptr(g), ctypes.byref(loss),
+                                  _stream(stream)))
+    return g, loss.value
 
 
 def ph_launch_counter():

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "handles.cuh"
+#include "mlp_handle.cuh"
 
 namespace phpp {
 
@@ -16,6 +17,7 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
 int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
 int count_within_device(const ph_leaves *lv, const ph_pairs *pr, cudaStream_t s);
+int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s);
 void fit_factor_poly(double U, int deg, float *coef);
 
 static thread_local char g_err[512] = "";
@@ -406,9 +408,30 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
     if (!pairs || pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
     if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
     if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
-    if (g_mode == PH_G_LEARNED) return fail(PH_ERR_ARG, "learned factor not available in this build");
-    (void)mlp;
+    if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP))
+        return fail(PH_ERR_ARG, "PH_G_LEARNED needs a ph_mlp handle");
     if (leaves->n > 0 && !acc) return fail(PH_ERR_ARG, "acc must not be NULL");
+    // the exact path judges the network: its validated error and the
+    // rcut / rs it was trained for decide whether it may stand in
+    bool use_learned = false;
+    char why[160] = "";
+    if (g_mode == PH_G_LEARNED) {
+        use_learned = true;
+        const double ratio = mlp->rcut / mlp->rs;
+        for (int b = 0; b < leaves->n_boxes && use_learned; b++) {
+            const BoxDev &bx = leaves->boxes_host[b];
+            const double rb = std::sqrt((double)bx.rcut2) / std::sqrt(-1.4426950408889634 / (4.0 * (double)bx.c_e));
+            if (std::fabs(rb / ratio - 1.0) > 1e-5) {
+                use_learned = false;
+                snprintf(why, sizeof why, "box %d has rcut/rs %.6g, the network was trained for %.6g", b, rb, ratio);
+            }
+        }
+        if (use_learned && !(mlp->max_rel_err <= mlp->tol)) {
+            use_learned = false;
+            snprintf(why, sizeof why, "validated network error %.3e above its tolerance %.1e", mlp->max_rel_err,
+                     mlp->tol);
+        }
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ph_pairs *pr = const_cast<ph_pairs *>(pairs);
     if (leaves->n == 0) return PH_OK;
@@ -420,10 +443,12 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
         if (rc) return rc;
         dacc = static_cast<float *>(pr->acc_tmp.p);
     }
-    rc = pp_exact_device(leaves, pairs, dacc, s);
+    rc = use_learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), dacc, s)
+                     : pp_exact_device(leaves, pairs, dacc, s);
     if (!rc && !dev)
         rc = cuda_check(cudaMemcpyAsync(acc, dacc, (size_t)leaves->n * 12, cudaMemcpyDeviceToHost, s), "copy acc");
     pr->last_stream = s;
+    if (!rc && g_mode == PH_G_LEARNED && !use_learned) return fail(PH_WARN_FALLBACK, "exact factor used: %s", why);
     return rc;
 }
 
@@ -450,6 +475,8 @@ void ph_free(void *handle)
         ph_pairs *h = static_cast<ph_pairs *>(handle);
         free_pairs(h);
         delete h;
+    } else if (kind == KIND_MLP) {
+        mlp_free(static_cast<ph_mlp *>(handle));
     }
 }
 
@@ -467,6 +494,7 @@ int ph_status(const void *handle)
         const ph_pairs *h = static_cast<const ph_pairs *>(handle);
         return read_status(h->status, h->last_stream);
     }
+    if (kind == KIND_MLP) return PH_OK;
     return fail(PH_ERR_STATE, "unknown handle");
 }
 

@@ -1,0 +1,176 @@
+// Device evaluation of the short-range factor: the exact form of Eq. (split)
+// (SFU + polynomial) and the learned 1-16-16-1 SiLU network (tensor cores).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "phpp_internal.cuh"
+
+namespace phpp {
+
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_sfu(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_sfu(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_sfu(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Exact factor f(r) = 2^(r^2 c_e) h(t), t = 2r/rcut - 1 (scalar form of the
+// PP kernel's evaluation).
+__device__ __forceinline__ float exact_factor(float r2, float t, const float *poly, int npoly, float c_e)
+{
+    float h = poly[npoly];
+    for (int q = npoly - 1; q >= 0; q--) h = fmaf(h, t, poly[q]);
+    return ex2_sfu(r2 * c_e) * h;
+}
+
+// silu(a) = a / (1 + e^-a) with SFU ex2 and rcp (relative error ~1e-7).
+__device__ __forceinline__ float silu_sfu(float a)
+{
+    return a * rcp_sfu(1.f + ex2_sfu(a * -1.4426950408889634f));
+}
+
+// Network parameters in the flat order W1[16], b1[16], W2[16][16] (row k =
+// weights into unit k), b2[16], W3[16], b3.
+constexpr int kMlpParams = 321;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi): ~16 significant bits.
+__device__ __forceinline__ void split_bf16(float x, float &hi, float &lo)
+{
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Per-lane share of the network for warp-level evaluation with
+// mma.sync.m16n8k16 (BF16 in, FP32 accumulate).  Lane = 4 g + q: the lane
+// owns rows g and g+8 of each 16-pair tile and hidden columns
+// {2q, 2q+1, 2q+8, 2q+9}; the 16x16 second layer is two n8 halves.
+struct MlpLane {
+    float w1[4], b1[4];          // layer 1 for the lane's 4 columns
+    uint32_t bhi[2][2], blo[2][2];   // W2^T fragments (hi / lo parts), per n-half
+    float b2[2][2];              // bias of output columns 8h + 2q, 8h + 2q + 1
+    float w3[2][2];              // W3 of the same columns
+    float b3;
+};
+
+__device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int cols[4] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        L.w1[c] = w[cols[c]];
+        L.b1[c] = w[16 + cols[c]];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int n = g + 8 * h;             // output unit of this B column
+        const float *row = w + 32 + 16 * n;  // W2[n][kk]
+        float hi[4], lo[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) split_bf16(row[cols[c]], hi[c], lo[c]);
+        L.bhi[h][0] = pack_bf16(hi[0], hi[1]);
+        L.bhi[h][1] = pack_bf16(hi[2], hi[3]);
+        L.blo[h][0] = pack_bf16(lo[0], lo[1]);
+        L.blo[h][1] = pack_bf16(lo[2], lo[3]);
+        L.b2[h][0] = w[288 + 8 * h + 2 * q];
+        L.b2[h][1] = w[288 + 8 * h + 2 * q + 1];
+        L.w3[h][0] = w[304 + 8 * h + 2 * q];
+        L.w3[h][1] = w[304 + 8 * h + 2 * q + 1];
+    }
+    L.b3 = w[320];
+}
+
+// The network's factor for the warp's 32 pairs: lane i passes the input
+// z0 = 2r/rcut - 1 of its pair and receives g_hat of its pair.  Layer 1 and
+// both SiLU layers in FP32 on the FMA/SFU pipes; layer 2 as BF16 tensor-core
+// MMAs with FP32 accumulation, activations and weights split into BF16
+// hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16 bits.
+__device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2;
+    float out = 0.f;
+#pragma unroll
+    for (int tile = 0; tile < 2; tile++) {
+        const float za = __shfl_sync(0xffffffffu, z0, 16 * tile + g);
+        const float zb = __shfl_sync(0xffffffffu, z0, 16 * tile + g + 8);
+        float ha[4], hb[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            ha[c] = silu_sfu(fmaf(L.w1[c], za, L.b1[c]));
+            hb[c] = silu_sfu(fmaf(L.w1[c], zb, L.b1[c]));
+        }
+        float ah[4][2], al[4][2];   // [reg][element]
+        split_bf16(ha[0], ah[0][0], al[0][0]); split_bf16(ha[1], ah[0][1], al[0][1]);   // row g, cols 2q..
+        split_bf16(hb[0], ah[1][0], al[1][0]); split_bf16(hb[1], ah[1][1], al[1][1]);   // row g+8
+        split_bf16(ha[2], ah[2][0], al[2][0]); split_bf16(ha[3], ah[2][1], al[2][1]);   // row g, cols 2q+8..
+        split_bf16(hb[2], ah[3][0], al[3][0]); split_bf16(hb[3], ah[3][1], al[3][1]);   // row g+8
+        uint32_t Ahi[4], Alo[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            Ahi[r] = pack_bf16(ah[r][0], ah[r][1]);
+            Alo[r] = pack_bf16(al[r][0], al[r][1]);
+        }
+        float ya = 0.f, yb = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            float d[4] = {L.b2[h][0], L.b2[h][1], L.b2[h][0], L.b2[h][1]};
+            mma_bf16(d, Alo, L.bhi[h][0], L.bhi[h][1]);
+            mma_bf16(d, Ahi, L.blo[h][0], L.blo[h][1]);
+            mma_bf16(d, Ahi, L.bhi[h][0], L.bhi[h][1]);
+            ya = fmaf(L.w3[h][0], silu_sfu(d[0]), ya);
+            ya = fmaf(L.w3[h][1], silu_sfu(d[1]), ya);
+            yb = fmaf(L.w3[h][0], silu_sfu(d[2]), yb);
+            yb = fmaf(L.w3[h][1], silu_sfu(d[3]), yb);
+        }
+        ya += __shfl_xor_sync(0xffffffffu, ya, 1);
+        ya += __shfl_xor_sync(0xffffffffu, ya, 2);
+        yb += __shfl_xor_sync(0xffffffffu, yb, 1);
+        yb += __shfl_xor_sync(0xffffffffu, yb, 2);
+        // pair p = 16 tile + rho is lane p; rows rho < 8 are held as ya, others
+        // as yb, by the quad 4 (rho % 8) .. 4 (rho % 8) + 3
+        const int rho = lane & 15;
+        const float va = __shfl_sync(0xffffffffu, ya, 4 * (rho & 7));
+        const float vb = __shfl_sync(0xffffffffu, yb, 4 * (rho & 7));
+        if ((lane >> 4) == tile) out = (rho < 8 ? va : vb) + L.b3;
+    }
+    return out;
+}
+
+}  // namespace phpp

@@ -16,6 +16,7 @@
 //   f(r) = 2^(r2 c_e) h(t),  t = r / (R_s U) - 1,  h a degree-NPOLY polynomial
 // with rsqrt (plus one Newton correction), sqrt and ex2 on the SFU.  Partial
 // sums over runs of 16 sources are added to the total with Kahan compensation.
+#include "factor.cuh"
 #include "handles.cuh"
 
 namespace phpp {
@@ -28,27 +29,6 @@ namespace {
 constexpr int kPPWarps = 8;
 constexpr int kPPThreads = kPPWarps * 32;
 constexpr int kJBuf = 256;      // staged sources per warp (even)
-
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float sqrt_sfu(float x)
-{
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float ex2_sfu(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 struct PPArgs {
     const BoxDev *boxes;
@@ -67,6 +47,7 @@ struct PPArgs {
     unsigned long long *n_inter;
     unsigned long long *n_staged;
     float *acc;
+    const float *mlp_w;      // learned factor weights [321] (learned kernel)
 };
 
 struct Kahan3 {
@@ -191,6 +172,36 @@ __device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int
     }
 }
 
+// Learned factor: one source per step for all 32 lanes (the network is
+// evaluated warp-wide on the tensor cores), runs of 16 sources per Kahan add.
+__device__ __forceinline__ void sum_buffer_learned(const float *Af, const float *Bf, int nbuf, const float4 xi,
+                                                   float eps2, float rcut2, float c_v, const MlpLane &L, Kahan3 &k)
+{
+    for (int j0 = 0; j0 < nbuf; j0 += 16) {
+        const int j1 = j0 + 16 < nbuf ? j0 + 16 : nbuf;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        for (int j = j0; j < j1; j++) {
+            const int m = j >> 1, sl = j & 1;
+            const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
+            const float mj = Bf[m * 4 + 2 + sl];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float x = r2 + eps2;
+            const float y = rsqrt_sfu(x);
+            const float y2 = y * y;
+            const float y3 = y2 * y;
+            const float inv3 = fmaf(y3, fmaf(x * -1.5f, y2, 1.5f), y3);
+            const float t = sqrt_sfu(r2 * c_v) - 1.f;
+            const float gh = mlp_warp_eval(t, L);
+            float w = (mj * gh) * inv3;
+            w = r2 < rcut2 ? w : 0.f;
+            px = fmaf(w, dx, px);
+            py = fmaf(w, dy, py);
+            pz = fmaf(w, dz, pz);
+        }
+        k.add(px, py, pz);
+    }
+}
+
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 {
 #pragma unroll
@@ -207,8 +218,8 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 // the entry of its particle by a binary search over the prefix sums, so that
 // every lane loads a useful particle whatever the leaf sizes.  Kept sources
 // are written as pairs into the warp's buffer; a full buffer is summed.
-template <int NPOLY>
-__global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp_exact(PPArgs a)
+template <int NPOLY, bool kLearned>
+__global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
     __shared__ float4 sB[kPPWarps][kJBuf / 2];
@@ -218,6 +229,8 @@ __global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp_exact(PPA
     float *Af = reinterpret_cast<float *>(A), *Bf = reinterpret_cast<float *>(Bq);
     const int ng = *a.n_groups;
     unsigned long long inter = 0, staged = 0;
+    MlpLane L;
+    if (kLearned) mlp_lane_load(a.mlp_w, L);
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(a.queue, 1);
@@ -289,7 +302,10 @@ __global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp_exact(PPA
                         }
                     }
                     __syncwarp();
-                    sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
+                    if (kLearned)
+                        sum_buffer_learned(Af, Bf, nbuf, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+                    else
+                        sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
                     inter += (unsigned long long)nbuf * ni;
                     staged += nbuf;
                     nbuf = 0;
@@ -313,7 +329,10 @@ __global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp_exact(PPA
             }
         }
         __syncwarp();
-        sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
+        if (kLearned)
+            sum_buffer_learned(Af, Bf, nbuf, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+        else
+            sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
         inter += (unsigned long long)nbuf * ni;
         staged += nbuf;
         __syncwarp();
@@ -431,18 +450,31 @@ static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArg
     a.acc = d_acc;
 }
 
+int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s)
+{
+    PPArgs a;
+    pp_args(lv, pr, d_acc, a);
+    a.mlp_w = mlp_w;
+    int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
+    if (rc) return rc;
+    k_pp<10, true><<<sm_count() * PHPP_PP_MIN_BLOCKS, kPPThreads, 0, s>>>(a);
+    count_launch();
+    return cuda_check(cudaGetLastError(), "learned pp kernel");
+}
+
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)
 {
     PPArgs a;
     pp_args(lv, pr, d_acc, a);
+    a.mlp_w = nullptr;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    const int grid = sm_count() * 4;
+    const int grid = sm_count() * PHPP_PP_MIN_BLOCKS;
     switch (lv->poly_degree) {
-    case 10: k_pp_exact<10><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 12: k_pp_exact<12><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 14: k_pp_exact<14><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 16: k_pp_exact<16><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 10: k_pp<10, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 12: k_pp<12, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 14: k_pp<14, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 16: k_pp<16, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
     default: return fail(PH_ERR_STATE, "unsupported polynomial degree %d", lv->poly_degree);
     }
     return cuda_check(cudaGetLastError(), "pp kernel");
