@@ -87,6 +87,9 @@ extern "C" {
  *             same tree with every octree level split into three binary
  *             levels along the key's x, y, z bits (leaves closer to
  *             leaf_max); 0 = default (1).
+ *   pp_variant PP kernel shape: 0 = two 8-warp blocks per SM (deeper
+ *             unrolled source loop), 1 = three blocks per SM (fewer
+ *             registers, more warps).  Same results.
  */
 typedef struct ph_params {
     double  L;
@@ -98,11 +101,14 @@ typedef struct ph_params {
     int32_t key_kind;
     int32_t group_size;
     int32_t level_bits;
+    int32_t pp_variant;
+    int32_t reserved;
 } ph_params;
 
 typedef struct ph_leaves ph_leaves;   /* sorted particles + leaf / group tables */
 typedef struct ph_pairs  ph_pairs;    /* cutoff leaf-pair list (CSR by group)    */
 typedef struct ph_mlp    ph_mlp;      /* learned short-range factor             */
+typedef struct ph_graph  ph_graph;    /* a whole step captured as a CUDA graph  */
 
 /*
  * Sort the particles of one box along the space-filling curve and cut them
@@ -172,7 +178,56 @@ int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n,
              const ph_params *params, int g_mode, const ph_mlp *mlp, float *acc,
              void *stream, ph_leaves **leaves, ph_pairs **pairs);
 
-/* Free any handle (ph_leaves, ph_pairs, ph_mlp).  NULL is a no-op. */
+/*
+ * Capture the whole step (build, pairs, PP) for these handles as one CUDA
+ * graph: one replay launches every kernel of the step -- the PP part one
+ * persistent launch over all boxes of a batched handle -- with no host
+ * synchronisation and no allocation (the batched, graph-captured execution
+ * of the many-box workload; Sec. 4.3's task queue over all boxes' groups).
+ *   leaves, pairs  built once before (ph_build_leaves[_batched], ph_leaf_pairs)
+ *                  for the same particle count and boxes.
+ *   d_pos, d_mass, d_acc  device buffers read / written at every replay.
+ *   headroom       the pair list gets a fixed capacity of
+ *                  (1 + headroom) x its current length (e.g. 0.25).
+ * Replays that would overflow it latch PH_ERR_CAPACITY in ph_status(pairs)
+ * (no entry beyond the capacity is written); rebuild the pairs and recreate
+ * the graph.  Learned mode with a network that fails its tolerance captures
+ * the exact factor and returns PH_WARN_FALLBACK.  Synchronises once.
+ */
+int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int pos_type, const float *d_mass,
+                    int g_mode, const ph_mlp *mlp, float *d_acc, double headroom, void *stream,
+                    ph_graph **graph);
+
+/* Replay a captured step on `stream` (asynchronous). */
+int ph_graph_launch(ph_graph *graph, void *stream);
+
+/* Kernels launched by one replay. */
+int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
+
+/*
+ * Autotuner: time the whole step (build, pairs, exact PP) for every
+ * combination of leaf_max in {16, 24, 32, 48, 64}, level_bits in {1, 3} and
+ * pp_variant in {0, 1} on the caller's particles (device buffers; boxes as
+ * for ph_build_leaves_batched, n_boxes = 1 for one box) and return the
+ * fastest as out->best (params[0] with the winning knobs), with every
+ * candidate's median of `reps` timed steps.  The knobs do not change the
+ * result beyond FP32 summation order.  Synchronises.
+ */
+#define PH_TUNE_MAX 32
+typedef struct ph_tune_result {
+    ph_params best;
+    float     best_ms;
+    int32_t   n_tried;
+    float     ms[PH_TUNE_MAX];
+    int32_t   leaf_max[PH_TUNE_MAX];
+    int32_t   level_bits[PH_TUNE_MAX];
+    int32_t   pp_variant[PH_TUNE_MAX];
+} ph_tune_result;
+
+int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int64_t *box_offsets, int32_t n_boxes,
+                const ph_params *params, int32_t reps, void *stream, ph_tune_result *out);
+
+/* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph).  NULL is a no-op. */
 void ph_free(void *handle);
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -41,7 +41,8 @@ class PhError(RuntimeError):
 class ph_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("G", ctypes.c_double), ("eps", ctypes.c_double),
                 ("rs", ctypes.c_double), ("rcut", ctypes.c_double), ("leaf_max", ctypes.c_int32),
-                ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("level_bits", ctypes.c_int32)]
+                ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("level_bits", ctypes.c_int32),
+                ("pp_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ph_leaves_view(ctypes.Structure):
@@ -62,6 +63,13 @@ class ph_train_params(ctypes.Structure):
 
 
 PH_MLP_PARAMS = 321
+PH_TUNE_MAX = 32
+
+
+class ph_tune_result(ctypes.Structure):
+    _fields_ = [("best", ph_params), ("best_ms", ctypes.c_float), ("n_tried", ctypes.c_int32),
+                ("ms", ctypes.c_float * PH_TUNE_MAX), ("leaf_max", ctypes.c_int32 * PH_TUNE_MAX),
+                ("level_bits", ctypes.c_int32 * PH_TUNE_MAX), ("pp_variant", ctypes.c_int32 * PH_TUNE_MAX)]
 
 
 class ph_pairs_view(ctypes.Structure):
@@ -97,6 +105,12 @@ _SIGS = {
                       ctypes.c_int),
     "ph_mlp_get": ([_VP, _VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "ph_mlp_loss_grad": ([_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_float), _VP], ctypes.c_int),
+    "ph_graph_create": ([_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP,
+                         ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
+    "ph_graph_kernels": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ph_autotune": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(ph_params),
+                     ctypes.c_int32, _VP, ctypes.POINTER(ph_tune_result)], ctypes.c_int),
 }
 
 
@@ -152,9 +166,10 @@ def _pos_type(t):
     raise TypeError("positions must be float32 or float64")
 
 
-def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0, level_bits=0):
+def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0, level_bits=0,
+                pp_variant=0):
     return ph_params(float(L), float(G), float(eps), float(rs), float(rcut), int(leaf_max), int(key_kind),
-                     int(group_size), int(level_bits))
+                     int(group_size), int(level_bits), int(pp_variant), 0)
 
 
 class Handle:
@@ -314,6 +329,36 @@ def ph_mlp_loss_grad(weights, z0, target, stream=None):
     _check(lib().ph_mlp_loss_grad(_ptr(w), _ptr(z), _ptr(t), int(z.size), _ptr(g), ctypes.byref(loss),
                                   _stream(stream)))
     return g, loss.value
+
+
+def ph_graph_create(leaves, pairs, pos, mass, g_mode, mlp, acc, headroom=0.25, stream=None):
+    """Capture build + pairs + PP for these handles as one CUDA graph."""
+    out = ctypes.c_void_p(None)
+    _check(lib().ph_graph_create(leaves.ptr, pairs.ptr, _ptr(pos), _pos_type(pos), _ptr(mass), int(g_mode),
+                                 mlp.ptr if mlp is not None else None, _ptr(acc), float(headroom), _stream(stream),
+                                 ctypes.byref(out)))
+    return Handle(out.value, (leaves, pairs, pos, mass, acc, mlp))
+
+
+def ph_graph_launch(graph, stream=None):
+    return _check(lib().ph_graph_launch(graph.ptr, _stream(stream)))
+
+
+def ph_graph_kernels(graph):
+    k = ctypes.c_int64(0)
+    _check(lib().ph_graph_kernels(graph.ptr, ctypes.byref(k)))
+    return k.value
+
+
+def ph_autotune(pos, mass, box_offsets, params_list, reps=3, stream=None):
+    """Time every tuner candidate on these particles; returns ph_tune_result."""
+    offs = np.ascontiguousarray(np.asarray(box_offsets, np.int64))
+    nb = offs.size - 1
+    arr = (ph_params * nb)(*params_list)
+    res = ph_tune_result()
+    _check(lib().ph_autotune(_ptr(pos), _pos_type(pos), _ptr(mass), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             nb, arr, int(reps), _stream(stream), ctypes.byref(res)))
+    return res
 
 
 def ph_launch_counter():

@@ -18,6 +18,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
 int count_within_device(const ph_leaves *lv, const ph_pairs *pr, cudaStream_t s);
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s);
+void graph_free(ph_graph *g);
 void fit_factor_poly(double U, int deg, float *coef);
 
 static thread_local char g_err[512] = "";
@@ -125,6 +126,7 @@ static int check_params(const ph_params &p, int b)
     if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "box %d: group_size must be 0 or 32", b);
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3)
         return fail(PH_ERR_ARG, "box %d: level_bits must be 0, 1 or 3", b);
+    if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "box %d: pp_variant must be 0 or 1", b);
     if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
         return fail(PH_ERR_ARG, "box %d: rcut/rs = %g above the supported 9.2", b, p.rcut / p.rs);
     return PH_OK;
@@ -164,8 +166,10 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         int rc = check_params(params[b], b);
         if (rc) return rc;
         if (params[b].leaf_max != params[0].leaf_max || params[b].key_kind != params[0].key_kind ||
-            params[b].group_size != params[0].group_size || params[b].level_bits != params[0].level_bits)
-            return fail(PH_ERR_ARG, "leaf_max, key_kind, group_size and level_bits must be the same for all boxes");
+            params[b].group_size != params[0].group_size || params[b].level_bits != params[0].level_bits ||
+            params[b].pp_variant != params[0].pp_variant)
+            return fail(PH_ERR_ARG,
+                        "leaf_max, key_kind, group_size, level_bits and pp_variant must be the same for all boxes");
     }
     ph_leaves *h = *leaves;
     if (h && h->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "handle is not a ph_leaves");
@@ -183,6 +187,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->key_kind = params[0].key_kind;
     h->group_size = params[0].group_size ? params[0].group_size : 32;
     h->level_bits = params[0].level_bits ? params[0].level_bits : 1;
+    h->pp_variant = params[0].pp_variant;
     h->boxes_host.resize(nb);
     int deg = 10;
     for (int b = 0; b < nb; b++) {
@@ -477,6 +482,8 @@ void ph_free(void *handle)
         delete h;
     } else if (kind == KIND_MLP) {
         mlp_free(static_cast<ph_mlp *>(handle));
+    } else if (kind == KIND_GRAPH) {
+        graph_free(static_cast<ph_graph *>(handle));
     }
 }
 
@@ -494,7 +501,7 @@ int ph_status(const void *handle)
         const ph_pairs *h = static_cast<const ph_pairs *>(handle);
         return read_status(h->status, h->last_stream);
     }
-    if (kind == KIND_MLP) return PH_OK;
+    if (kind == KIND_MLP || kind == KIND_GRAPH) return PH_OK;
     return fail(PH_ERR_STATE, "unknown handle");
 }
 

@@ -1,0 +1,124 @@
+// A whole step captured once as a CUDA graph and replayed.
+//
+// The capture records every kernel of the step -- keys, radix sort, leaves,
+// groups, frames, pair count / scan / fill and the persistent PP kernel over
+// all boxes -- with the handles' buffers at fixed addresses and the pair list
+// at a fixed capacity, so a replay needs no host round trip and no
+// allocation.  Positions and masses are read from the captured device
+// pointers at every replay (update them in place between replays).  A replay
+// whose pair list would outgrow the capacity writes no entry beyond it and
+// latches PH_ERR_CAPACITY in the pairs handle's status (ph_status); rebuild
+// with ph_leaf_pairs and create a new graph then.
+#include <new>
+
+#include "handles.cuh"
+#include "mlp_handle.cuh"
+
+namespace phpp {
+int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float *mass, cudaStream_t s);
+int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
+int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
+int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s);
+}  // namespace phpp
+
+struct ph_graph {
+    uint32_t kind = phpp::KIND_GRAPH;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;        // our kernel launches per replay
+};
+
+using namespace phpp;
+
+namespace phpp {
+void graph_free(ph_graph *g)
+{
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+}  // namespace phpp
+
+extern "C" {
+
+int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int pos_type, const float *d_mass,
+                    int g_mode, const ph_mlp *mlp, float *d_acc, double headroom, void *stream, ph_graph **out)
+{
+    if (!leaves || leaves->kind != KIND_LEAVES || !pairs || pairs->kind != KIND_PAIRS || !out)
+        return fail(PH_ERR_ARG, "ph_graph_create: leaves, pairs and out must be valid");
+    if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    if (leaves->n > 0 && (!d_pos || !d_acc || !is_device_ptr(d_pos) || !is_device_ptr(d_acc) ||
+                          (d_mass && !is_device_ptr(d_mass))))
+        return fail(PH_ERR_ARG, "ph_graph_create: pos, mass and acc must be device memory");
+    if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "bad pos_type");
+    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "bad g_mode");
+    if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP)) return fail(PH_ERR_ARG, "learned mode needs mlp");
+    if (!(headroom >= 0 && headroom < 100)) return fail(PH_ERR_ARG, "headroom must be in [0, 100)");
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    // fixed pair capacity with headroom over the current list
+    const int64_t want = (int64_t)((double)pairs->n_pairs * (1.0 + headroom)) + 1024;
+    if (want > pairs->capacity) {
+        int rc = cuda_check(cudaStreamSynchronize(caller), "sync before growing");
+        if (!rc) rc = ensure(pairs->entries, (size_t)want * sizeof(float4));
+        if (rc) return rc;
+        pairs->capacity = want;
+    }
+    pairs->fixed_capacity = true;
+    bool learned = false;
+    if (g_mode == PH_G_LEARNED) {
+        learned = mlp->max_rel_err <= mlp->tol;
+    }
+    ph_graph *g = new (std::nothrow) ph_graph();
+    if (!g) return fail(PH_ERR_OOM, "host allocation failed");
+    cudaStream_t s = nullptr;
+    int rc = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "create capture stream");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(caller), "sync before capture");
+    const long long k0 = ph_launch_counter();
+    if (!rc) rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (!rc) {
+        int rc2 = cuda_check(cudaMemsetAsync(leaves->status.p, 0, 4, s), "clear status");
+        if (!rc2) rc2 = cuda_check(cudaMemsetAsync(pairs->status.p, 0, 4, s), "clear status");
+        if (!rc2) rc2 = build_leaves_device(leaves, d_pos, pos_type, d_mass, s);
+        if (!rc2) rc2 = build_pairs_device(leaves, pairs, s, false);
+        if (!rc2 && leaves->n > 0)
+            rc2 = learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), d_acc, s)
+                          : pp_exact_device(leaves, pairs, d_acc, s);
+        cudaGraph_t gr = nullptr;
+        rc = cuda_check(cudaStreamEndCapture(s, &gr), "end capture");
+        g->graph = gr;
+        if (!rc) rc = rc2;
+    }
+    g->kernels = ph_launch_counter() - k0;
+    if (!rc) rc = cuda_check(cudaGraphInstantiate(&g->exec, g->graph, 0), "instantiate");
+    if (s) cudaStreamDestroy(s);
+    if (rc) {
+        graph_free(g);
+        return rc;
+    }
+    // the capture only recorded the launches; do not count them as run
+    count_launch((int)-g->kernels);
+    leaves->last_stream = caller;
+    pairs->last_stream = caller;
+    *out = g;
+    if (g_mode == PH_G_LEARNED && !learned)
+        return fail(PH_WARN_FALLBACK, "exact factor captured: validated network error %.3e above %.1e",
+                    mlp->max_rel_err, mlp->tol);
+    return PH_OK;
+}
+
+int ph_graph_launch(ph_graph *g, void *stream)
+{
+    if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
+    int rc = cuda_check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "graph launch");
+    if (!rc) count_launch((int)g->kernels);
+    return rc;
+}
+
+int ph_graph_kernels(const ph_graph *g, int64_t *kernels)
+{
+    if (!g || g->kind != KIND_GRAPH || !kernels) return fail(PH_ERR_ARG, "bad arguments");
+    *kernels = g->kernels;
+    return PH_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@ struct ph_leaves {
     int32_t max_leaf = 32;
     int32_t key_kind = PH_KEY_MORTON;
     int32_t level_bits = 1;      // key bits per level of the leaf hierarchy (1 or 3)
+    int32_t pp_variant = 0;      // PP kernel register/occupancy variant (0: 2 blocks/SM, 1: 3)
     std::vector<phpp::BoxDev> boxes_host;
     // device buffers
     phpp::DevBuf boxes;          // BoxDev[n_boxes]

@@ -112,6 +112,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT) return fail(PH_ERR_ARG, "unknown key_kind");
     if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "group_size must be 0 or 32");
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3) return fail(PH_ERR_ARG, "level_bits must be 0, 1 or 3");
+    if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "pp_variant must be 0 or 1");
     const int deg = degree_for(p.rcut / (2.0 * p.rs));
     if (deg < 0) return fail(PH_ERR_ARG, "rcut/rs = %g above the supported 9.2", p.rcut / p.rs);
     if (n == 0) return PH_OK;
@@ -166,6 +167,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     lv.max_leaf = p.leaf_max;
     lv.key_kind = p.key_kind;
     lv.level_bits = p.level_bits ? p.level_bits : 1;
+    lv.pp_variant = p.pp_variant == 1 ? 1 : 0;
     const size_t N = (size_t)n;
     Carver c{static_cast<char *>(base)};
     c.take(lv.boxes, sizeof(BoxDev));

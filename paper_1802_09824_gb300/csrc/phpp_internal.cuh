@@ -48,7 +48,12 @@ enum : uint32_t {
 };
 
 // ---------------------------------------------------------------- handles
-enum HandleKind : uint32_t { KIND_LEAVES = 0x4c454146u, KIND_PAIRS = 0x50414952u, KIND_MLP = 0x4d4c5021u };
+enum HandleKind : uint32_t {
+    KIND_LEAVES = 0x4c454146u,
+    KIND_PAIRS = 0x50414952u,
+    KIND_MLP = 0x4d4c5021u,
+    KIND_GRAPH = 0x47524150u,
+};
 
 struct DevBuf {
     void *p = nullptr;

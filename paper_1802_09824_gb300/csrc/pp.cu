@@ -22,10 +22,6 @@
 namespace phpp {
 namespace {
 
-#ifndef PHPP_PP_MIN_BLOCKS
-#define PHPP_PP_MIN_BLOCKS 2   // resident 8-warp blocks per SM the register budget must allow
-#endif
-
 constexpr int kPPWarps = 8;
 constexpr int kPPThreads = kPPWarps * 32;
 constexpr int kJBuf = 256;      // staged sources per warp (even)
@@ -218,8 +214,10 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 // the entry of its particle by a binary search over the prefix sums, so that
 // every lane loads a useful particle whatever the leaf sizes.  Kept sources
 // are written as pairs into the warp's buffer; a full buffer is summed.
-template <int NPOLY, bool kLearned>
-__global__ void __launch_bounds__(kPPThreads, PHPP_PP_MIN_BLOCKS) k_pp(PPArgs a)
+// kMinBlocks: resident 8-warp blocks per SM the register budget must allow
+// (2: up to 128 registers, deeper unrolled pair loop; 3: up to 80).
+template <int NPOLY, bool kLearned, int kMinBlocks>
+__global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
     __shared__ float4 sB[kPPWarps][kJBuf / 2];
@@ -457,7 +455,7 @@ int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_
     a.mlp_w = mlp_w;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    k_pp<10, true><<<sm_count() * PHPP_PP_MIN_BLOCKS, kPPThreads, 0, s>>>(a);
+    k_pp<10, true, 2><<<sm_count() * 2, kPPThreads, 0, s>>>(a);
     count_launch();
     return cuda_check(cudaGetLastError(), "learned pp kernel");
 }
@@ -469,12 +467,18 @@ int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaS
     a.mlp_w = nullptr;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    const int grid = sm_count() * PHPP_PP_MIN_BLOCKS;
-    switch (lv->poly_degree) {
-    case 10: k_pp<10, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 12: k_pp<12, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 14: k_pp<14, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 16: k_pp<16, false><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    const int mb = lv->pp_variant == 1 ? 3 : 2;
+    const int grid = sm_count() * mb;
+    const int key = lv->poly_degree * 10 + mb;
+    switch (key) {
+    case 102: k_pp<10, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 122: k_pp<12, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 142: k_pp<14, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 162: k_pp<16, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 103: k_pp<10, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 123: k_pp<12, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 143: k_pp<14, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
+    case 163: k_pp<16, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
     default: return fail(PH_ERR_STATE, "unsupported polynomial degree %d", lv->poly_degree);
     }
     return cuda_check(cudaGetLastError(), "pp kernel");

@@ -1,0 +1,123 @@
+"""Batched boxes, the graph-captured step, kernel variants and the autotuner."""
+import numpy as np
+import pytest
+
+from helpers import check_parity, gpu_accel, oracle_accel
+from paper_1802_09824_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _tensors(ps):
+    import torch
+    return (torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(),
+            torch.zeros((ps.n, 3), dtype=torch.float32, device="cuda"))
+
+
+def _params(B, ps, **kw):
+    return [B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, kw.get("leaf_max", 32), 0, 0,
+                          kw.get("level_bits", 0), kw.get("pp_variant", 0)) for bp in ps.boxes]
+
+
+@pytest.mark.parametrize("nboxes", [1, 12])
+def test_graph_replay_matches_direct_calls(gpu_lib, nboxes):
+    import torch
+    B = gpu_lib
+    ps = (synth.workload("uniform_small", scale=5000) if nboxes == 1
+          else synth.batch_boxes(nboxes, seed=5, n_min=300, n_max=5000))
+    pos, mass, acc = _tensors(ps)
+    prm = _params(B, ps)
+    lv = B.ph_build_leaves_batched(pos, mass, ps.offsets, prm)
+    pr = B.ph_leaf_pairs(lv)
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc)
+    torch.cuda.synchronize()
+    direct = acc.cpu().numpy().copy()
+    g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.25)
+    assert B.ph_graph_kernels(g) > 10
+    for _ in range(2):
+        acc.zero_()
+        B.ph_graph_launch(g)
+        torch.cuda.synchronize()
+        B.ph_status(pr)
+        np.testing.assert_array_equal(acc.cpu().numpy(), direct)
+    # new positions written in place are picked up by the next replay
+    rng = np.random.default_rng(3)
+    moved = ps.pos + rng.uniform(-1e-3, 1e-3, ps.pos.shape).astype(np.float32)
+    moved = np.mod(moved, 1.0).astype(np.float32)
+    pos.copy_(torch.from_numpy(moved))
+    B.ph_graph_launch(g)
+    torch.cuda.synchronize()
+    B.ph_status(pr)
+    ps2 = synth.ParticleSet(moved, ps.mass, ps.boxes, ps.offsets, "moved")
+    for b in range(min(nboxes, 3)):
+        sl = ps2.box_slice(b)
+        check_parity(acc.cpu().numpy()[sl], oracle_accel(ps2, box=b))
+    for h in (g, pr, lv):
+        B.ph_free(h)
+
+
+def test_graph_capacity_overflow_is_latched(gpu_lib):
+    import torch
+    B = gpu_lib
+    ps = synth.workload("uniform_small", scale=6000)
+    pos, mass, acc = _tensors(ps)
+    prm = _params(B, ps)
+    lv = B.ph_build_leaves(pos, mass, prm[0])
+    pr = B.ph_leaf_pairs(lv)
+    g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.0)
+    # the same particles squeezed into a corner need many more leaf pairs
+    squeezed = (ps.pos * 0.15).astype(np.float32)
+    pos.copy_(torch.from_numpy(squeezed))
+    B.ph_graph_launch(g)
+    torch.cuda.synchronize()
+    with pytest.raises(B.PhError) as ei:
+        B.ph_status(pr)
+    assert ei.value.code == B.PH_ERR_CAPACITY
+    B.ph_free(g)
+    # rebuilding sizes the list again and the result is right
+    lv = B.ph_build_leaves(pos, mass, prm[0], leaves=lv)
+    pr2 = B.ph_leaf_pairs(lv)
+    B.ph_pp_accel(lv, pr2, B.PH_G_EXACT, None, acc)
+    torch.cuda.synchronize()
+    sq = synth._single(squeezed, ps.mass, ps.boxes[0], "sq")
+    check_parity(acc.cpu().numpy(), oracle_accel(sq))
+    for h in (pr2, pr, lv):
+        B.ph_free(h)
+
+
+def test_kernel_variants_give_identical_forces(gpu_lib):
+    ps = synth.workload("nfw_mix_256", scale=24)
+    a, l1, p1 = gpu_accel(gpu_lib, ps)
+    import torch
+    B = gpu_lib
+    pos, mass, acc = _tensors(ps)
+    prm = _params(B, ps, pp_variant=1)
+    lv = B.ph_build_leaves(pos, mass, prm[0])
+    pr = B.ph_leaf_pairs(lv)
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(acc.cpu().numpy(), a)
+    for h in (pr, lv, p1, l1):
+        B.ph_free(h)
+
+
+def test_autotuner_picks_a_tried_candidate(gpu_lib, tmp_path):
+    import torch
+    B = gpu_lib
+    from paper_1802_09824_gb300 import tuning
+    ps = synth.workload("zeldovich_128", scale=32)
+    pos, mass, acc = _tensors(ps)
+    prm = _params(B, ps)
+    res = B.ph_autotune(pos, mass, ps.offsets, prm, reps=1)
+    assert res.n_tried == 20
+    ms = np.array(res.ms[:res.n_tried])
+    assert np.all(ms > 0) and abs(res.best_ms - ms.min()) < 1e-6
+    k = int(np.argmin(ms))
+    assert (res.best.leaf_max, res.best.level_bits, res.best.pp_variant) == (
+        res.leaf_max[k], res.level_bits[k], res.pp_variant[k])
+    p2, info = tuning.tuned(B, pos, mass, ps.offsets, _params(B, ps), reps=1, path=str(tmp_path / "t.json"))
+    assert info["cache"] == "miss"
+    got, lv, pr = gpu_accel(B, ps, leaf_max=p2[0].leaf_max, level_bits=p2[0].level_bits)
+    check_parity(got, oracle_accel(ps))
+    B.ph_free(pr)
+    B.ph_free(lv)
