@@ -150,6 +150,107 @@ def _oracle_rate(ps, seconds, seed=5):
     return float(r.n_within.sum()) / dt, nt, dt, force.num_threads()
 
 
+def _learned_extra(B, ps, lv, pr, stream, t_exact_pp):
+    """The learned factor on the same lists: training, time, errors."""
+    import torch
+    from oracle import force
+    bp = ps.boxes[0]
+    tp = B.make_train_params(n_samples=1_000_000, batch=8192, steps=100_000, lr0=3e-3, lr_min=3e-6, tol=1e-3,
+                             seed=2024)
+    t0 = time.perf_counter()
+    mlp = B.ph_mlp_train(tp, bp.rs, bp.rcut)
+    train_s = time.perf_counter() - t0
+    w, err, loss = B.ph_mlp_get(mlp)
+    # time the learned kernel whatever the judge says (tolerance 1)
+    timed = B.ph_mlp_create(w, bp.rs, bp.rcut, tol=1.0)
+    acc_l = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
+    acc_e = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc_e, stream)
+    B.ph_pp_accel(lv, pr, B.PH_G_LEARNED, timed, acc_l, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        B.ph_pp_accel(lv, pr, B.PH_G_LEARNED, timed, acc_l, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_l = e0.elapsed_time(e1) / reps
+    rng = np.random.default_rng(11)
+    tg = rng.choice(ps.n, 256, replace=False)
+    ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=tg)
+    am = np.linalg.norm(ref.acc, axis=1)
+    tau = 1e-3 * np.median(am)
+
+    def p99(a):
+        e = np.linalg.norm(a[tg].astype(np.float64) - ref.acc, axis=1) / np.maximum(am, tau)
+        return float(np.percentile(e, 99))
+
+    out = {"config": "learned factor on the same workload and lists (MLP 1-16-16-1 SiLU, BF16 MMA layer 2)",
+           "train_steps": tp.steps, "train_batch": tp.batch, "train_s": train_s, "train_loss": loss,
+           "g_max_rel_err": err, "judge_tolerance": 1e-3, "falls_back": bool(err > 1e-3),
+           "pp_ms": t_l, "exact_pp_ms": t_exact_pp, "speedup_vs_exact": t_exact_pp / t_l,
+           "force_p99_rel_err_learned": p99(acc_l.cpu().numpy()),
+           "force_p99_rel_err_exact": p99(acc_e.cpu().numpy()), "oracle_targets": int(tg.size)}
+    B.ph_free(timed)
+    B.ph_free(mlp)
+    return out
+
+
+def _batched_extra(B, args, dev, stream):
+    """512 boxes: one graph-captured step vs one ph_accel call per box."""
+    import torch
+    from paper_1802_09824_gb300 import synth
+    ps = synth.workload("batch_512")
+    prms = [_params(B, bp, args.leaf_max or 32, args.key) for bp in ps.boxes]
+    pos = torch.from_numpy(ps.pos).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    lv = B.ph_build_leaves_batched(pos, mass, ps.offsets, prms, stream)
+    pr = B.ph_leaf_pairs(lv, stream)
+    n_within = B.ph_count_within(lv, pr, stream)
+    g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, 0.25, stream)
+    kernels = B.ph_graph_kernels(g)
+    for _ in range(3):
+        B.ph_graph_launch(g, stream)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        B.ph_graph_launch(g, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.ph_status(pr)
+    t_graph = e0.elapsed_time(e1) / reps
+    # the same boxes one call each (handles reused per box)
+    handles = [(None, None)] * len(ps.boxes)
+    views = [(pos[ps.box_slice(b)], mass[ps.box_slice(b)], acc[ps.box_slice(b)]) for b in range(len(ps.boxes))]
+
+    def per_box():
+        for b, (p_, m_, a_) in enumerate(views):
+            l_, r_ = handles[b]
+            handles[b] = B.ph_accel(p_, m_, prms[b], B.PH_G_EXACT, None, a_, stream, leaves=l_, pairs=r_)
+
+    per_box()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        per_box()
+    torch.cuda.synchronize()
+    t_box = 1e3 * (time.perf_counter() - t0) / 2
+    for l_, r_ in handles:
+        B.ph_free(r_)
+        B.ph_free(l_)
+    B.ph_free(g)
+    B.ph_free(pr)
+    B.ph_free(lv)
+    return {"workload": "batch_512", "n": ps.n, "boxes": len(ps.boxes), "interactions_within_rcut": n_within,
+            "graph_ms_per_step": t_graph, "graph_kernels_per_step": kernels,
+            "per_box_calls_ms_per_step": t_box, "speedup_graph_vs_per_box": t_box / t_graph,
+            "value_graph": n_within / (t_graph * 1e-3), "unit": UNIT}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -215,6 +316,11 @@ def run_ours(args, rank, world, local_rank):
     prm = _params(B, bp, args.leaf_max, args.key)
     pos = torch.from_numpy(ps.pos).to(dev)
     mass = torch.from_numpy(ps.mass).to(dev)
+    tune_info = None
+    if not args.leaf_max and not args.no_tune:
+        # leaf size / hierarchy / kernel shape from the in-project autotuner
+        from paper_1802_09824_gb300 import tuning
+        (prm,), tune_info = tuning.tuned(B, pos, mass, ps.offsets, [prm], reps=3)
     acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -315,6 +421,12 @@ def run_ours(args, rank, world, local_rank):
                (t_pp * 1e-3) / 1e12},
         "build_and_pairs_ms": t_step - t_pp,
     }
+    if tune_info is not None:
+        line["config"]["tuned"] = {"leaf_max": prm.leaf_max, "level_bits": prm.level_bits,
+                                   "pp_variant": prm.pp_variant, "cache": tune_info["cache"]}
+    if not args.no_extras:
+        line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
+        line["batched"] = _batched_extra(B, args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, nt, dt, cores = _oracle_rate(ps, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -340,6 +452,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the learned-factor and 512-box measurements")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (leaf_max 32)")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -41,9 +41,11 @@ def ground_level(L: float, rcut: float) -> int:
 
 
 def wrap(x, L):
-    """Wrap coordinates into [0, L): x - L floor(x/L), in float64."""
+    """Wrap coordinates into [0, L): x - L floor(x/L), in float64; values
+    already in [0, L) are kept as they are."""
     x = np.asarray(x, np.float64)
-    return x - L * np.floor(x / L)
+    inside = (x >= 0.0) & (x < L)
+    return np.where(inside, x, x - L * np.floor(x / L))
 
 
 def quantise(xw, L, T):

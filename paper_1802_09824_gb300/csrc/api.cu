@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, handle management, host/device
 // staging.  Every step of the computation runs in the kernels of build.cu,
 // pairs.cu and pp.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -182,7 +183,23 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->n = n;
     h->n_boxes = nb;
-    h->key_bits = key_bits_per_axis(nb);
+    {
+        // key bits per axis: enough for cells ~128 times finer than the mean
+        // spacing of the most populated box (deeper cells never hold more
+        // than leaf_max particles outside strong clustering; cells that do
+        // are cut into runs), capped by the 63-bit key and at least 4 bits
+        // below the ground grid
+        int64_t nmax = 1;
+        int gmax = 0;
+        for (int b = 0; b < nb; b++) {
+            nmax = std::max<int64_t>(nmax, box_offsets[b + 1] - box_offsets[b]);
+            gmax = std::max(gmax, ground_level(params[b].L, params[b].rcut));
+        }
+        int lg = 0;
+        while ((int64_t)1 << (3 * lg) < nmax) lg++;     // ceil(log2(cbrt(nmax)))
+        const int cap = key_bits_per_axis(nb);
+        h->key_bits = std::min(cap, std::max(lg + 7, gmax + 4));
+    }
     h->max_leaf = params[0].leaf_max;
     h->key_kind = params[0].key_kind;
     h->group_size = params[0].group_size ? params[0].group_size : 32;

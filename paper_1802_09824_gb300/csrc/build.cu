@@ -41,7 +41,10 @@ __device__ __forceinline__ int find_box(const int32_t *box_first, int nb, int64_
 
 __device__ __forceinline__ double wrap_coord(double x, double L)
 {
-    // x - L floor(x / L), each operation rounded once (no contraction)
+    // x - L floor(x / L), each operation rounded once (no contraction); a
+    // coordinate already in [0, L) is returned as is, which is what the
+    // formula gives for it (floor = 0), without the FP64 divide
+    if (x >= 0.0 && x < L) return x;
     double f = floor(__ddiv_rn(x, L));
     return __dsub_rn(x, __dmul_rn(L, f));
 }
@@ -425,7 +428,9 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
                                                status);
         count_launch();
         bool alt = false;
-        int bits = 3 * T + (nb > 1 ? (int)std::ceil(std::log2((double)nb)) : 0);
+        int box_bits = 0;
+        while ((1 << box_bits) < nb) box_bits++;
+        int bits = 3 * T + box_bits;
         bits = (bits + kSortBits - 1) / kSortBits * kSortBits;
         int rc = radix_sort_pairs(keys, vals, static_cast<uint64_t *>(h->keys_alt.p),
                                   static_cast<int32_t *>(h->vals_alt.p), n, bits, h->temp.p, s, &alt);
