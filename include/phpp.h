@@ -80,8 +80,10 @@ extern "C" {
  *   leaf_max  largest number of particles in an octree leaf, 1..256 (the
  *             N_pp of Sec. 3.1 / leaf size of Sec. 4.4).
  *   key_kind  PH_KEY_MORTON or PH_KEY_HILBERT.
- *   group_size number of target particles summed together by one warp:
- *             0 (default) or 32.
+ *   group_size target particles summed together by one warp: 32, 16 or 8
+ *             (then 2 or 4 lanes share a target, each taking every 2nd or
+ *             4th source; smaller groups waste fewer pairs beyond rcut);
+ *             0 = default (32).
  *   level_bits key bits per level of the leaf hierarchy: 3 = octree cells
  *             (each level splits a cell into 8 children, Sec. 3.2), 1 = the
  *             same tree with every octree level split into three binary
@@ -147,8 +149,9 @@ int ph_build_leaves_batched(const void *pos, int pos_type, const float *mass,
  * 27 ground cells around it (Sec. 4.3: a ground cell and its 26 neighbours,
  * each with the periodic image its offset implies) whose bounding box comes
  * within rcut of the group's bounding box (Sec. 3.3: leaf-leaf interactions
- * go to the PP kernel).  Stored per entry: the leaf and the FP32 offset
- * (leaf reference - group reference, computed in FP64, image included).
+ * go to the PP kernel).  Stored per entry: the FP32 offset (leaf reference -
+ * group reference, computed in FP64, image included), the leaf's first
+ * particle and its particle count.
  * Synchronises the stream once to size the list, unless the handle was given
  * a fixed capacity with ph_pairs_reserve (then overflow is latched as
  * PH_ERR_CAPACITY and no entry beyond the capacity is written).
@@ -206,8 +209,8 @@ int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
 
 /*
  * Autotuner: time the whole step (build, pairs, exact PP) for every
- * combination of leaf_max in {16, 24, 32, 48, 64}, level_bits in {1, 3} and
- * pp_variant in {0, 1} on the caller's particles (device buffers; boxes as
+ * combination of leaf_max in {32, 64}, level_bits in {1, 3}, pp_variant in
+ * {0, 1} and group_size in {8, 16, 32} on the caller's particles (device buffers; boxes as
  * for ph_build_leaves_batched, n_boxes = 1 for one box) and return the
  * fastest as out->best (params[0] with the winning knobs), with every
  * candidate's median of `reps` timed steps.  The knobs do not change the
@@ -222,6 +225,7 @@ typedef struct ph_tune_result {
     int32_t   leaf_max[PH_TUNE_MAX];
     int32_t   level_bits[PH_TUNE_MAX];
     int32_t   pp_variant[PH_TUNE_MAX];
+    int32_t   group_size[PH_TUNE_MAX];
 } ph_tune_result;
 
 int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int64_t *box_offsets, int32_t n_boxes,
@@ -267,7 +271,9 @@ typedef struct ph_pairs_view {
     int32_t n_groups;
     int32_t reserved;
     const int64_t *group_off;  /* [n_groups+1] CSR offsets                     */
-    const float   *entries;    /* [n_pairs*4] off.x, off.y, off.z, leaf (bits) */
+    const float   *entries;    /* [n_pairs*4] off.x, off.y, off.z, and the     */
+                               /* leaf's first particle (int32 bits, sorted)   */
+    const uint8_t *counts;     /* [n_pairs] particles in the leaf minus one    */
 } ph_pairs_view;
 
 int ph_leaves_get_view(const ph_leaves *leaves, ph_leaves_view *out);

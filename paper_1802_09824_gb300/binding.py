@@ -69,12 +69,13 @@ PH_TUNE_MAX = 32
 class ph_tune_result(ctypes.Structure):
     _fields_ = [("best", ph_params), ("best_ms", ctypes.c_float), ("n_tried", ctypes.c_int32),
                 ("ms", ctypes.c_float * PH_TUNE_MAX), ("leaf_max", ctypes.c_int32 * PH_TUNE_MAX),
-                ("level_bits", ctypes.c_int32 * PH_TUNE_MAX), ("pp_variant", ctypes.c_int32 * PH_TUNE_MAX)]
+                ("level_bits", ctypes.c_int32 * PH_TUNE_MAX), ("pp_variant", ctypes.c_int32 * PH_TUNE_MAX),
+                ("group_size", ctypes.c_int32 * PH_TUNE_MAX)]
 
 
 class ph_pairs_view(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p)]
+                ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
 
 
 _lib = None
@@ -376,7 +377,7 @@ def _dev(ptr, shape, typestr):
     import torch
     if int(np.prod(shape)) == 0 or not ptr:
         dt = {"<u8": torch.int64, "<i4": torch.int32, "<f8": torch.float64, "<f4": torch.float32,
-              "<i8": torch.int64}[typestr]
+              "<i8": torch.int64, "|u1": torch.uint8}[typestr]
         return torch.zeros(shape, dtype=dt, device="cuda")
     return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
 
@@ -410,4 +411,5 @@ def ph_pairs_get_view(pairs):
         "n_pairs": v.n_pairs, "n_groups": v.n_groups,
         "group_off": _dev(v.group_off, (v.n_groups + 1,), "<i8"),
         "entries": _dev(v.entries, (v.n_pairs, 4), "<f4"),
+        "counts": _dev(v.counts, (v.n_pairs,), "|u1"),
     }

@@ -124,7 +124,8 @@ static int check_params(const ph_params &p, int b)
     if (p.leaf_max < 1 || p.leaf_max > kMaxLeaf) return fail(PH_ERR_ARG, "box %d: leaf_max must be 1..%d", b, kMaxLeaf);
     if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT)
         return fail(PH_ERR_ARG, "box %d: unknown key_kind %d", b, p.key_kind);
-    if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "box %d: group_size must be 0 or 32", b);
+    if (p.group_size != 0 && p.group_size != 8 && p.group_size != 16 && p.group_size != 32)
+        return fail(PH_ERR_ARG, "box %d: group_size must be 0, 8, 16 or 32", b);
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3)
         return fail(PH_ERR_ARG, "box %d: level_bits must be 0, 1 or 3", b);
     if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "box %d: pp_variant must be 0 or 1", b);
@@ -145,7 +146,8 @@ static void free_leaves(ph_leaves *h)
 
 static void free_pairs(ph_pairs *h)
 {
-    DevBuf *bufs[] = {&h->group_cnt, &h->group_off, &h->entries, &h->work, &h->status, &h->temp, &h->acc_tmp};
+    DevBuf *bufs[] = {&h->group_cnt, &h->group_off, &h->entries, &h->ecount, &h->work, &h->status, &h->temp,
+                      &h->acc_tmp};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -202,7 +204,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     }
     h->max_leaf = params[0].leaf_max;
     h->key_kind = params[0].key_kind;
-    h->group_size = params[0].group_size ? params[0].group_size : 32;
+    h->group_size = params[0].group_size ? params[0].group_size : kDefaultGroup;
     h->level_bits = params[0].level_bits ? params[0].level_bits : 1;
     h->pp_variant = params[0].pp_variant;
     h->boxes_host.resize(nb);
@@ -373,6 +375,7 @@ int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity)
         if (!p) return fail(PH_ERR_OOM, "host allocation failed");
     }
     int rc = ensure(p->entries, (size_t)(capacity > 0 ? capacity : 1) * sizeof(float4));
+    if (!rc) rc = ensure(p->ecount, (size_t)(capacity > 0 ? capacity : 1));
     if (rc) {
         if (fresh) delete p;
         return rc;
@@ -407,6 +410,7 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
     }
     if (!rc && !p->entries.p) {
         rc = ensure(p->entries, 16 * 1024);
+        if (!rc) rc = ensure(p->ecount, 1024);
         if (!rc) p->capacity = 1024;
     }
     if (!rc) rc = build_pairs_device(leaves, p, s, !p->fixed_capacity);
@@ -573,6 +577,7 @@ int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
     out->n_groups = ng;
     out->group_off = static_cast<const int64_t *>(p->group_off.p);
     out->entries = static_cast<const float *>(p->entries.p);
+    out->counts = static_cast<const uint8_t *>(p->ecount.p);
     return PH_OK;
 }
 

@@ -1,6 +1,8 @@
-// In-project autotuner: leaf size, leaf hierarchy and PP kernel shape.
+// In-project autotuner: leaf size, leaf hierarchy, target group size and PP
+// kernel shape.
 //
-// Every candidate (leaf_max x level_bits x pp_variant) runs the whole step on
+// Every candidate (leaf_max x level_bits x pp_variant x group_size) runs the
+// whole step on
 // the caller's particles -- build, pairs, PP -- once to warm up and then
 // `reps` times under CUDA events; the candidate with the smallest median
 // step time wins.  The result does not depend on the knobs (only the FP32
@@ -30,9 +32,10 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
     if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
-    const int leaf_sizes[] = {16, 24, 32, 48, 64};
+    const int leaf_sizes[] = {32, 64};
     const int levels[] = {1, 3};
     const int variants[] = {0, 1};
+    const int groups[] = {8, 16, 32};
     std::vector<ph_params> prm(params, params + n_boxes);
     memset(out, 0, sizeof *out);
     out->best_ms = 3.0e38f;
@@ -40,12 +43,14 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
     ph_pairs *pr = nullptr;
     for (int lm : leaf_sizes)
         for (int lb : levels)
-            for (int pv : variants) {
+            for (int pv : variants)
+            for (int gs : groups) {
                 if (rc || out->n_tried >= PH_TUNE_MAX) break;
                 for (auto &p : prm) {
                     p.leaf_max = lm;
                     p.level_bits = lb;
                     p.pp_variant = pv;
+                    p.group_size = gs;
                 }
                 std::vector<float> ms;
                 for (int r = 0; !rc && r <= reps; r++) {
@@ -67,6 +72,7 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
                 out->leaf_max[k] = lm;
                 out->level_bits[k] = lb;
                 out->pp_variant[k] = pv;
+                out->group_size[k] = gs;
                 if (med < out->best_ms) {
                     out->best_ms = med;
                     out->best = prm[0];

@@ -60,6 +60,7 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     if (want > pairs->capacity) {
         int rc = cuda_check(cudaStreamSynchronize(caller), "sync before growing");
         if (!rc) rc = ensure(pairs->entries, (size_t)want * sizeof(float4));
+        if (!rc) rc = ensure(pairs->ecount, (size_t)want);
         if (rc) return rc;
         pairs->capacity = want;
     }

@@ -58,7 +58,8 @@ struct ph_pairs {
     const ph_leaves *built_from = nullptr;
     phpp::DevBuf group_cnt;      // int64[n + 1]
     phpp::DevBuf group_off;      // int64[n + 1]
-    phpp::DevBuf entries;        // float4[capacity]
+    phpp::DevBuf entries;        // float4[capacity]: offset xyz, first source particle
+    phpp::DevBuf ecount;         // uint8[capacity]: particles in the entry's leaf - 1
     phpp::DevBuf work;           // int32 queue counter + int64 work counters
     phpp::DevBuf status;         // uint32
     phpp::DevBuf temp;

@@ -207,6 +207,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     c.take(pr.temp, tscan);
     const int64_t cap = (int64_t)PH_NOALLOC_PAIRS_PER_PARTICLE * n;
     c.take(pr.entries, 16 * (size_t)cap);
+    c.take(pr.ecount, (size_t)cap);
     if (c.over) return fail(PH_ERR_CAPACITY, "ph_accel_noalloc: fixed scratch too small for n = %lld", (long long)n);
     pr.capacity = cap;
     pr.fixed_capacity = true;

@@ -29,7 +29,9 @@ struct PairArgs {
     const double *leaf_ref;
     int64_t *cnt;            // count pass output [n_groups]
     const int64_t *off;      // fill pass input   [n_groups + 1]
-    float4 *ent;             // fill pass output
+    float4 *ent;             // fill pass output: offset x, y, z, first source particle (bits)
+    uint8_t *ecnt;           // fill pass output: particles in the leaf - 1
+    const int32_t *leaf_first;
     int64_t cap;
     uint32_t *status;
 };
@@ -132,8 +134,10 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                     e.x = __double2float_rn((lr[0] + sx * L) - gref[0]);
                     e.y = __double2float_rn((lr[1] + sy * L) - gref[1]);
                     e.z = __double2float_rn((lr[2] + sz * L) - gref[2]);
-                    e.w = __int_as_float(l);
+                    const int f0 = a.leaf_first[l];
+                    e.w = __int_as_float(f0);
                     a.ent[pos] = e;
+                    a.ecnt[pos] = (uint8_t)(a.leaf_first[l + 1] - f0 - 1);
                 } else {
                     atomicOr(a.status, ST_CAPACITY);
                 }
@@ -160,6 +164,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.leaf_c4 = static_cast<const float4 *>(lv->leaf_c4.p);
     a.leaf_h4 = static_cast<const float4 *>(lv->leaf_h4.p);
     a.leaf_ref = static_cast<const double *>(lv->leaf_ref.p);
+    a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
     a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
     a.off = static_cast<const int64_t *>(pr->group_off.p);
     a.status = static_cast<uint32_t *>(pr->status.p);
@@ -187,11 +192,13 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
         if (total > pr->capacity) {
             int64_t cap = total + total / 8 + 1024;
             rc = ensure(pr->entries, (size_t)cap * sizeof(float4));
+            if (!rc) rc = ensure(pr->ecount, (size_t)cap);
             if (rc) return rc;
             pr->capacity = cap;
         }
     }
     a.ent = static_cast<float4 *>(pr->entries.p);
+    a.ecnt = static_cast<uint8_t *>(pr->ecount.p);
     a.cap = pr->capacity;
     k_pairs<true><<<grid, kThreads, 0, s>>>(a);
     count_launch();

@@ -16,6 +16,7 @@ constexpr int kMaxLeaf = 256;         // largest leaf_max accepted
 constexpr int kGroundMax = 7;         // N_side <= 2^7 per box
 constexpr int kSortBits = 8;          // radix digit width
 constexpr int kThreads = 256;
+constexpr int kDefaultGroup = 32;   // target group size when ph_params.group_size = 0
 
 // Per-box constants, one record per box in device memory.
 struct BoxDev {

@@ -16,6 +16,8 @@
 //   f(r) = 2^(r2 c_e) h(t),  t = r / (R_s U) - 1,  h a degree-NPOLY polynomial
 // with rsqrt (plus one Newton correction), sqrt and ex2 on the SFU.  Partial
 // sums over runs of 16 sources are added to the total with Kahan compensation.
+#include <cstring>
+
 #include "factor.cuh"
 #include "handles.cuh"
 
@@ -25,6 +27,15 @@ namespace {
 constexpr int kPPWarps = 8;
 constexpr int kPPThreads = kPPWarps * 32;
 constexpr int kJBuf = 256;      // staged sources per warp (even)
+
+typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pair
+
+// Constants of one box, each duplicated into both halves of a pair.
+struct PairConsts {
+    f2_t poly[kMaxPoly + 1];
+    f2_t eps2, c_v, c_e, m15, c15, m1;
+    float rcut2, rfilt2;
+};
 
 struct PPArgs {
     const BoxDev *boxes;
@@ -37,13 +48,17 @@ struct PPArgs {
     const int32_t *leaf_first;
     const int32_t *perm;
     const int64_t *group_off;
-    const float4 *entries;
+    const float4 *entries;   // offset xyz, first source particle (bits)
+    const uint8_t *ecount;   // particles in the entry's leaf - 1
     int64_t cap;             // entries written (reads stop there)
     int32_t *queue;
     unsigned long long *n_inter;
     unsigned long long *n_staged;
     float *acc;
     const float *mlp_w;      // learned factor weights [321] (learned kernel)
+    // constants shared by every box (the uniform kernels read them straight
+    // from the parameter bank instead of holding them in registers)
+    PairConsts uc;
 };
 
 struct Kahan3 {
@@ -58,7 +73,6 @@ struct Kahan3 {
 };
 
 // ---- packed FP32 pairs (f32x2, sm_100+): two sources per instruction
-typedef unsigned long long f2_t;
 
 __device__ __forceinline__ f2_t pk(float lo, float hi)
 {
@@ -103,19 +117,12 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
     return r;
 }
 
-// Constants of one box, each duplicated into both halves of a pair.
-template <int NPOLY>
-struct PairConsts {
-    f2_t poly[NPOLY + 1];
-    f2_t eps2, c_v, c_e, m15, c15, m1;
-    float rcut2;
-};
 
 // Two sources (A = x0 x1 y0 y1, B = z0 z1 m0 m1) against one target: add
 // m_j f(r) d / (r^2 + eps^2)^{3/2} into the pair accumulators.
 template <int NPOLY>
 __device__ __forceinline__ void interact2(const float4 a, const float4 b, const f2_t xi, const f2_t yi, const f2_t zi,
-                                          const PairConsts<NPOLY> &c, f2_t &px, f2_t &py, f2_t &pz)
+                                          const PairConsts &c, f2_t &px, f2_t &py, f2_t &pz)
 {
     const f2_t dx = sub2(pk(a.x, a.y), xi), dy = sub2(pk(a.z, a.w), yi), dz = sub2(pk(b.x, b.y), zi);
     f2_t r2 = mul2(dx, dx);
@@ -145,38 +152,52 @@ __device__ __forceinline__ void interact2(const float4 a, const float4 b, const 
     pz = fma2(wm, dz, pz);
 }
 
-// Sum a staged buffer of npair source pairs: plain FP32 partial sums over
-// runs of kRun pairs (16 sources), each run added to the target's total
-// with Kahan compensation.
+// Sum a staged buffer of npair source pairs.  With kSplit lanes per target
+// (target groups of 32 / kSplit particles) lane slot h takes the pairs
+// h, h + kSplit, h + 2 kSplit, ...; the buffer is padded with massless
+// sources to a whole number of pairs per slot.  Plain FP32 partial sums over
+// runs of kRun pairs, each run added to the lane's total with Kahan
+// compensation.
 constexpr int kRun = 8;
 
-template <int NPOLY>
-__device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int npair, const f2_t xi, const f2_t yi,
-                                           const f2_t zi, const PairConsts<NPOLY> &c, Kahan3 &k)
+template <int NPOLY, int kSplit>
+__device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int npair, int h, const f2_t xi,
+                                           const f2_t yi, const f2_t zi, const PairConsts &c, Kahan3 &k)
 {
-    int m = 0;
-    for (; m + kRun <= npair; m += kRun) {
+    const int nstep = npair / kSplit;
+    int s = 0;
+    for (; s + kRun <= nstep; s += kRun) {
         f2_t px = 0ull, py = 0ull, pz = 0ull;
 #pragma unroll 4
-        for (int u = 0; u < kRun; u++) interact2<NPOLY>(A[m + u], B[m + u], xi, yi, zi, c, px, py, pz);
+        for (int u = 0; u < kRun; u++) {
+            const int m = (s + u) * kSplit + h;
+            interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
+        }
         k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
     }
-    if (m < npair) {
+    if (s < nstep) {
         f2_t px = 0ull, py = 0ull, pz = 0ull;
-        for (; m < npair; m++) interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
+        for (; s < nstep; s++) {
+            const int m = s * kSplit + h;
+            interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
+        }
         k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
     }
 }
 
-// Learned factor: one source per step for all 32 lanes (the network is
-// evaluated warp-wide on the tensor cores), runs of 16 sources per Kahan add.
-__device__ __forceinline__ void sum_buffer_learned(const float *Af, const float *Bf, int nbuf, const float4 xi,
+// Learned factor: one source per lane and step (the network is evaluated
+// warp-wide on the tensor cores, so every lane takes part in every step),
+// runs of 16 steps per Kahan add.
+template <int kSplit>
+__device__ __forceinline__ void sum_buffer_learned(const float *Af, const float *Bf, int nbuf, int h, const float4 xi,
                                                    float eps2, float rcut2, float c_v, const MlpLane &L, Kahan3 &k)
 {
-    for (int j0 = 0; j0 < nbuf; j0 += 16) {
-        const int j1 = j0 + 16 < nbuf ? j0 + 16 : nbuf;
+    const int nstep = nbuf / kSplit;
+    for (int j0 = 0; j0 < nstep; j0 += 16) {
+        const int j1 = j0 + 16 < nstep ? j0 + 16 : nstep;
         float px = 0.f, py = 0.f, pz = 0.f;
-        for (int j = j0; j < j1; j++) {
+        for (int jj = j0; jj < j1; jj++) {
+            const int j = jj * kSplit + h;
             const int m = j >> 1, sl = j & 1;
             const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
             const float mj = Bf[m * 4 + 2 + sl];
@@ -198,6 +219,23 @@ __device__ __forceinline__ void sum_buffer_learned(const float *Af, const float 
     }
 }
 
+// Pad the staged sources with massless ones (at the group's reference point)
+// to a multiple of 2 kSplit; returns the padded count.
+template <int kSplit>
+__device__ __forceinline__ int pad_sources(float *Af, float *Bf, int nbuf, int lane)
+{
+    const int padded = (nbuf + 2 * kSplit - 1) / (2 * kSplit) * (2 * kSplit);
+    const int j = nbuf + lane;
+    if (j < padded) {
+        const int m = j >> 1, sl = j & 1;
+        Af[m * 4 + sl] = 0.f;
+        Af[m * 4 + 2 + sl] = 0.f;
+        Bf[m * 4 + sl] = 0.f;
+        Bf[m * 4 + 2 + sl] = 0.f;
+    }
+    return padded;
+}
+
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 {
 #pragma unroll
@@ -208,6 +246,51 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
     return v;
 }
 
+// 32 consecutive pair entries, one per lane, with the exclusive prefix sums
+// of their leaf sizes.
+struct EntryBatch {
+    float4 ent;
+    int l0, excl, total;
+    __device__ __forceinline__ void load(const PPArgs &a, int64_t eb, int64_t e1, int lane)
+    {
+        const int64_t e = eb + lane;
+        int cnt = 0;
+        ent = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < e1) {
+            ent = a.entries[e];
+            cnt = (int)a.ecount[e] + 1;
+        }
+        l0 = __float_as_int(ent.w);
+        const int incl = warp_incl_scan_i(cnt, lane);
+        excl = incl - cnt;
+        total = __shfl_sync(0xffffffffu, incl, 31);
+    }
+};
+
+// One staging round: the particle each lane loads (in flight until used) and
+// the offset of its entry.
+struct Round {
+    float4 p;
+    float ox, oy, oz;
+    bool valid;
+    __device__ __forceinline__ void issue(const PPArgs &a, const EntryBatch &b, int q0, int lane)
+    {
+        const int q = q0 + lane;
+        int o = 0;   // the lane whose entry holds concatenated particle q
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int ex = __shfl_sync(0xffffffffu, b.excl, o + step);
+            if (ex <= q) o += step;
+        }
+        const int j = __shfl_sync(0xffffffffu, b.l0, o) + (q - __shfl_sync(0xffffffffu, b.excl, o));
+        ox = __shfl_sync(0xffffffffu, b.ent.x, o);
+        oy = __shfl_sync(0xffffffffu, b.ent.y, o);
+        oz = __shfl_sync(0xffffffffu, b.ent.z, o);
+        valid = q < b.total;
+        p = valid ? a.pos_leaf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+};
+
 // Source staging and summation for one target group.  Entries are taken 32
 // at a time, one per lane; the lanes' leaf sizes are prefix-summed and the
 // concatenated source particles are loaded 32 per round, each lane finding
@@ -216,7 +299,10 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 // are written as pairs into the warp's buffer; a full buffer is summed.
 // kMinBlocks: resident 8-warp blocks per SM the register budget must allow
 // (2: up to 128 registers, deeper unrolled pair loop; 3: up to 80).
-template <int NPOLY, bool kLearned, int kMinBlocks>
+// kSplit: lanes per target (target groups of 32 / kSplit particles).
+// kUniform: every box has the same factor constants, read from the kernel's
+// parameter bank (no registers); else they are loaded per group.
+template <int NPOLY, bool kLearned, int kMinBlocks, int kSplit, bool kUniform>
 __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
@@ -236,55 +322,43 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         if (g >= ng) break;
         const int i0 = a.group_first[g], ni = a.group_first[g + 1] - i0;
         const BoxDev &bx = a.boxes[a.group_box[g]];
-        PairConsts<NPOLY> c;
+        PairConsts cl;
+        if (!kUniform) {
 #pragma unroll
-        for (int q = 0; q <= NPOLY; q++) c.poly[q] = pk(bx.poly[q], bx.poly[q]);
-        c.eps2 = pk(bx.eps2, bx.eps2);
-        c.c_v = pk(bx.c_v, bx.c_v);
-        c.c_e = pk(bx.c_e, bx.c_e);
-        c.m15 = pk(-1.5f, -1.5f);
-        c.c15 = pk(1.5f, 1.5f);
-        c.m1 = pk(-1.f, -1.f);
-        c.rcut2 = bx.rcut2;
-        const float rf2 = bx.rfilt2;
+            for (int q = 0; q <= NPOLY; q++) cl.poly[q] = pk(bx.poly[q], bx.poly[q]);
+            cl.eps2 = pk(bx.eps2, bx.eps2);
+            cl.c_v = pk(bx.c_v, bx.c_v);
+            cl.c_e = pk(bx.c_e, bx.c_e);
+            cl.m15 = pk(-1.5f, -1.5f);
+            cl.c15 = pk(1.5f, 1.5f);
+            cl.m1 = pk(-1.f, -1.f);
+            cl.rcut2 = bx.rcut2;
+            cl.rfilt2 = bx.rfilt2;
+        }
+        const PairConsts &c = kUniform ? a.uc : cl;
+        const float rf2 = c.rfilt2;
         const float4 gh = a.group_h4[g];
-        const float4 xi4 = lane < ni ? a.pos_group[i0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        constexpr int G = 32 / kSplit;
+        const int ti = lane & (G - 1), hs = lane / G;   // target slot, source slot
+        const float4 xi4 = ti < ni ? a.pos_group[i0 + ti] : make_float4(0.f, 0.f, 0.f, 0.f);
         const f2_t xi = pk(xi4.x, xi4.x), yi = pk(xi4.y, xi4.y), zi = pk(xi4.z, xi4.z);
         Kahan3 k;
         int nbuf = 0;
         const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
+        // Entries are taken 32 at a time; each round loads 32 concatenated
+        // source particles of the batch, one per lane.
         for (int64_t eb = a.group_off[g]; eb < e1; eb += 32) {
-            const int64_t e = eb + lane;
-            float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
-            int l0 = 0, cnt = 0;
-            if (e < e1) {
-                ent = a.entries[e];
-                const int leaf = __float_as_int(ent.w);
-                l0 = a.leaf_first[leaf];
-                cnt = a.leaf_first[leaf + 1] - l0;
-            }
-            const int incl = warp_incl_scan_i(cnt, lane);
-            const int excl = incl - cnt;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int q0 = 0; q0 < total; q0 += 32) {
-                const int q = q0 + lane;
-                int o = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int ex = __shfl_sync(0xffffffffu, excl, o + step);
-                    if (ex <= q) o += step;
-                }
-                const int j = __shfl_sync(0xffffffffu, l0, o) + (q - __shfl_sync(0xffffffffu, excl, o));
-                const float ox = __shfl_sync(0xffffffffu, ent.x, o);
-                const float oy = __shfl_sync(0xffffffffu, ent.y, o);
-                const float oz = __shfl_sync(0xffffffffu, ent.z, o);
-                float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            EntryBatch bt;
+            bt.load(a, eb, e1, lane);
+            for (int q0 = 0; q0 < bt.total; q0 += 32) {
+                Round cur;
+                cur.issue(a, bt, q0, lane);
+                float4 p = cur.p;
                 bool keep = false;
-                if (q < total) {
-                    p = a.pos_leaf[j];
-                    p.x = __fadd_rn(p.x, ox);
-                    p.y = __fadd_rn(p.y, oy);
-                    p.z = __fadd_rn(p.z, oz);
+                if (cur.valid) {
+                    p.x = __fadd_rn(p.x, cur.ox);
+                    p.y = __fadd_rn(p.y, cur.oy);
+                    p.z = __fadd_rn(p.z, cur.oz);
                     const float qx = fmaxf(fabsf(p.x) - gh.x, 0.f);
                     const float qy = fmaxf(fabsf(p.y) - gh.y, 0.f);
                     const float qz = fmaxf(fabsf(p.z) - gh.z, 0.f);
@@ -293,17 +367,12 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 const int nk = __popc(bal);
                 if (nbuf + nk > kJBuf) {
-                    if (nbuf & 1) {   // pad to a whole pair with a massless source
-                        if (lane == 0) {
-                            Af[(nbuf >> 1) * 4 + 1] = 0.f; Af[(nbuf >> 1) * 4 + 3] = 0.f;
-                            Bf[(nbuf >> 1) * 4 + 1] = 0.f; Bf[(nbuf >> 1) * 4 + 3] = 0.f;
-                        }
-                    }
+                    const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
                     __syncwarp();
                     if (kLearned)
-                        sum_buffer_learned(Af, Bf, nbuf, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+                        sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
                     else
-                        sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
+                        sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
                     inter += (unsigned long long)nbuf * ni;
                     staged += nbuf;
                     nbuf = 0;
@@ -320,26 +389,29 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                 nbuf += nk;
             }
         }
-        if (nbuf & 1) {
-            if (lane == 0) {
-                Af[(nbuf >> 1) * 4 + 1] = 0.f; Af[(nbuf >> 1) * 4 + 3] = 0.f;
-                Bf[(nbuf >> 1) * 4 + 1] = 0.f; Bf[(nbuf >> 1) * 4 + 3] = 0.f;
-            }
-        }
+        const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
         __syncwarp();
         if (kLearned)
-            sum_buffer_learned(Af, Bf, nbuf, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+            sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
         else
-            sum_buffer<NPOLY>(A, Bq, (nbuf + 1) >> 1, xi, yi, zi, c, k);
+            sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
         inter += (unsigned long long)nbuf * ni;
         staged += nbuf;
         __syncwarp();
-        if (lane < ni) {
-            const int64_t o = a.perm[i0 + lane];
-            const float G = bx.G;
-            a.acc[3 * o + 0] = G * (k.sx - k.cx);
-            a.acc[3 * o + 1] = G * (k.sy - k.cy);
-            a.acc[3 * o + 2] = G * (k.sz - k.cz);
+        // the kSplit source slots of a target add up their compensated totals
+        float tx = k.sx - k.cx, ty = k.sy - k.cy, tz = k.sz - k.cz;
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            tx += __shfl_xor_sync(0xffffffffu, tx, o);
+            ty += __shfl_xor_sync(0xffffffffu, ty, o);
+            tz += __shfl_xor_sync(0xffffffffu, tz, o);
+        }
+        if (hs == 0 && ti < ni) {
+            const int64_t o = a.perm[i0 + ti];
+            const float Gc = bx.G;
+            a.acc[3 * o + 0] = Gc * tx;
+            a.acc[3 * o + 1] = Gc * ty;
+            a.acc[3 * o + 2] = Gc * tz;
         }
     }
     if (lane == 0 && inter) {
@@ -371,9 +443,9 @@ __global__ void __launch_bounds__(kPPThreads) k_count_within(PPArgs a)
         const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
         for (int64_t e = a.group_off[g]; e < e1; e++) {
             const float4 ent = a.entries[e];
-            const int leaf = __float_as_int(ent.w);
-            const int j1 = a.leaf_first[leaf + 1];
-            for (int jb = a.leaf_first[leaf]; jb < j1; jb += 32) {
+            const int j0 = __float_as_int(ent.w);
+            const int j1 = j0 + (int)a.ecount[e] + 1;
+            for (int jb = j0; jb < j1; jb += 32) {
                 const int j = jb + lane;
                 const bool ok = j < j1;
                 float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -440,12 +512,24 @@ static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArg
     a.perm = static_cast<const int32_t *>(lv->keys_in_alt ? lv->vals_alt.p : lv->vals.p);
     a.group_off = static_cast<const int64_t *>(pr->group_off.p);
     a.entries = static_cast<const float4 *>(pr->entries.p);
+    a.ecount = static_cast<const uint8_t *>(pr->ecount.p);
     a.cap = pr->capacity;
     char *work = static_cast<char *>(pr->work.p);
     a.queue = reinterpret_cast<int32_t *>(work);
     a.n_inter = reinterpret_cast<unsigned long long *>(work + 8);
     a.n_staged = reinterpret_cast<unsigned long long *>(work + 16);
     a.acc = d_acc;
+}
+
+template <bool kLearned, int kMinBlocks, int kSplit, bool kUniform>
+static void launch_pp(int npoly, int grid, cudaStream_t s, const PPArgs &a)
+{
+    switch (npoly) {
+    case 10: k_pp<10, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    case 12: k_pp<12, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    case 14: k_pp<14, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    default: k_pp<16, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    }
 }
 
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s)
@@ -455,9 +539,43 @@ int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_
     a.mlp_w = mlp_w;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    k_pp<10, true, 2><<<sm_count() * 2, kPPThreads, 0, s>>>(a);
+    const int grid = sm_count() * 2;
+    if (lv->group_size == 8) k_pp<10, true, 2, 4, false><<<grid, kPPThreads, 0, s>>>(a);
+    else if (lv->group_size == 16) k_pp<10, true, 2, 2, false><<<grid, kPPThreads, 0, s>>>(a);
+    else k_pp<10, true, 2, 1, false><<<grid, kPPThreads, 0, s>>>(a);
     count_launch();
     return cuda_check(cudaGetLastError(), "learned pp kernel");
+}
+
+// true if every box has the same factor constants (then the kernel reads
+// them from its parameter bank)
+static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
+{
+    if ((int)lv->boxes_host.size() < lv->n_boxes || lv->n_boxes < 1) return false;   // no host copy of the boxes
+    const BoxDev &b0 = lv->boxes_host[0];
+    for (int b = 1; b < lv->n_boxes; b++) {
+        const BoxDev &bx = lv->boxes_host[b];
+        if (memcmp(bx.poly, b0.poly, sizeof b0.poly) || bx.eps2 != b0.eps2 || bx.c_v != b0.c_v ||
+            bx.c_e != b0.c_e || bx.rcut2 != b0.rcut2 || bx.rfilt2 != b0.rfilt2)
+            return false;
+    }
+    auto dup = [](float v) {
+        uint64_t u;
+        uint32_t bits;
+        memcpy(&bits, &v, 4);
+        u = ((uint64_t)bits << 32) | bits;
+        return (f2_t)u;
+    };
+    for (int q = 0; q <= kMaxPoly; q++) uc.poly[q] = dup(b0.poly[q]);
+    uc.eps2 = dup(b0.eps2);
+    uc.c_v = dup(b0.c_v);
+    uc.c_e = dup(b0.c_e);
+    uc.m15 = dup(-1.5f);
+    uc.c15 = dup(1.5f);
+    uc.m1 = dup(-1.f);
+    uc.rcut2 = b0.rcut2;
+    uc.rfilt2 = b0.rfilt2;
+    return true;
 }
 
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)
@@ -467,20 +585,31 @@ int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaS
     a.mlp_w = nullptr;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    const int mb = lv->pp_variant == 1 ? 3 : 2;
-    const int grid = sm_count() * mb;
-    const int key = lv->poly_degree * 10 + mb;
-    switch (key) {
-    case 102: k_pp<10, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 122: k_pp<12, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 142: k_pp<14, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 162: k_pp<16, false, 2><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 103: k_pp<10, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 123: k_pp<12, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 143: k_pp<14, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    case 163: k_pp<16, false, 3><<<grid, kPPThreads, 0, s>>>(a); count_launch(); break;
-    default: return fail(PH_ERR_STATE, "unsupported polynomial degree %d", lv->poly_degree);
+    const int npoly = lv->poly_degree;
+    if (npoly != 10 && npoly != 12 && npoly != 14 && npoly != 16)
+        return fail(PH_ERR_STATE, "unsupported polynomial degree %d", npoly);
+    const bool uni = uniform_consts(lv, a.uc);
+    const bool three = lv->pp_variant == 1;
+    const int grid = sm_count() * (three ? 3 : 2);
+    const int gs = lv->group_size;
+    if (uni) {
+        if (three) {
+            if (gs == 8) launch_pp<false, 3, 4, true>(npoly, grid, s, a);
+            else if (gs == 16) launch_pp<false, 3, 2, true>(npoly, grid, s, a);
+            else launch_pp<false, 3, 1, true>(npoly, grid, s, a);
+        } else {
+            if (gs == 8) launch_pp<false, 2, 4, true>(npoly, grid, s, a);
+            else if (gs == 16) launch_pp<false, 2, 2, true>(npoly, grid, s, a);
+            else launch_pp<false, 2, 1, true>(npoly, grid, s, a);
+        }
+    } else {
+        // boxes with different constants: the two-block shape only
+        const int g2 = sm_count() * 2;
+        if (gs == 8) launch_pp<false, 2, 4, false>(npoly, g2, s, a);
+        else if (gs == 16) launch_pp<false, 2, 2, false>(npoly, g2, s, a);
+        else launch_pp<false, 2, 1, false>(npoly, g2, s, a);
     }
+    count_launch();
     return cuda_check(cudaGetLastError(), "pp kernel");
 }
 

@@ -12,7 +12,7 @@ import json
 import math
 import os
 
-KNOBS = ("leaf_max", "level_bits", "pp_variant")
+KNOBS = ("leaf_max", "level_bits", "pp_variant", "group_size")
 
 
 def default_cache_path() -> str:
@@ -77,6 +77,6 @@ def tuned(B, pos, mass, box_offsets, params_list, reps=3, path=None, retune=Fals
     res = B.ph_autotune(pos, mass, box_offsets, params_list, reps)
     knobs = {k: int(getattr(res.best, k)) for k in KNOBS}
     tried = [{"leaf_max": res.leaf_max[i], "level_bits": res.level_bits[i], "pp_variant": res.pp_variant[i],
-              "ms": float(res.ms[i])} for i in range(res.n_tried)]
+              "group_size": res.group_size[i], "ms": float(res.ms[i])} for i in range(res.n_tried)]
     store(key, knobs, float(res.best_ms), path)
     return apply(params_list, knobs), {"cache": "miss", "key": key, "ms": float(res.best_ms), "tried": tried}

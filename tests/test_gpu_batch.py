@@ -85,6 +85,20 @@ def test_graph_capacity_overflow_is_latched(gpu_lib):
         B.ph_free(h)
 
 
+@pytest.mark.parametrize("gs", [8, 16, 32])
+def test_group_sizes_match_the_oracle(gpu_lib, gs):
+    ps = synth.workload("zeldovich_128", scale=32)
+    got, lv, pr = gpu_accel(gpu_lib, ps, group_size=gs)
+    check_parity(got, oracle_accel(ps))
+    gpu_lib.ph_free(pr)
+    gpu_lib.ph_free(lv)
+    nfw = synth.workload("nfw_mix_256", scale=20)
+    got, lv, pr = gpu_accel(gpu_lib, nfw, group_size=gs, level_bits=3)
+    check_parity(got, oracle_accel(nfw))
+    gpu_lib.ph_free(pr)
+    gpu_lib.ph_free(lv)
+
+
 def test_kernel_variants_give_identical_forces(gpu_lib):
     ps = synth.workload("nfw_mix_256", scale=24)
     a, l1, p1 = gpu_accel(gpu_lib, ps)
@@ -109,15 +123,16 @@ def test_autotuner_picks_a_tried_candidate(gpu_lib, tmp_path):
     pos, mass, acc = _tensors(ps)
     prm = _params(B, ps)
     res = B.ph_autotune(pos, mass, ps.offsets, prm, reps=1)
-    assert res.n_tried == 20
+    assert res.n_tried == 24
     ms = np.array(res.ms[:res.n_tried])
     assert np.all(ms > 0) and abs(res.best_ms - ms.min()) < 1e-6
     k = int(np.argmin(ms))
-    assert (res.best.leaf_max, res.best.level_bits, res.best.pp_variant) == (
-        res.leaf_max[k], res.level_bits[k], res.pp_variant[k])
+    assert (res.best.leaf_max, res.best.level_bits, res.best.pp_variant, res.best.group_size) == (
+        res.leaf_max[k], res.level_bits[k], res.pp_variant[k], res.group_size[k])
     p2, info = tuning.tuned(B, pos, mass, ps.offsets, _params(B, ps), reps=1, path=str(tmp_path / "t.json"))
     assert info["cache"] == "miss"
-    got, lv, pr = gpu_accel(B, ps, leaf_max=p2[0].leaf_max, level_bits=p2[0].level_bits)
+    got, lv, pr = gpu_accel(B, ps, leaf_max=p2[0].leaf_max, level_bits=p2[0].level_bits,
+                            group_size=p2[0].group_size)
     check_parity(got, oracle_accel(ps))
     B.ph_free(pr)
     B.ph_free(lv)

@@ -31,10 +31,10 @@ def _snapped(centre, half):
     return ref, np.maximum(hi - ref, ref - lo)
 
 
-def _build(B, ps, kind=0, leaf_max=16, level_bits=1):
+def _build(B, ps, kind=0, leaf_max=16, level_bits=1, group_size=32):
     import torch
     bp = ps.boxes[0]
-    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max, kind, 0, level_bits)
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max, kind, group_size, level_bits)
     lv = B.ph_build_leaves(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm)
     torch.cuda.synchronize()
     return lv, B.ph_leaves_get_view(lv)
@@ -47,8 +47,9 @@ def _build(B, ps, kind=0, leaf_max=16, level_bits=1):
 def test_keys_sort_leaves_groups_bit_exact(gpu_lib, kind, clustered, n, level_bits):
     B = gpu_lib
     ps = _set(n=n, clustered=clustered)
-    lv, v = _build(B, ps, kind, level_bits=level_bits)
-    t = T.BoxTree(ps.pos, 1.0, ps.boxes[0].rcut, 16, 32, kind, T=v["key_bits"], level_bits=level_bits)
+    gs = (8, 16, 32)[n % 3]
+    lv, v = _build(B, ps, kind, level_bits=level_bits, group_size=gs)
+    t = T.BoxTree(ps.pos, 1.0, ps.boxes[0].rcut, 16, gs, kind, T=v["key_bits"], level_bits=level_bits)
     assert v["n_leaves"] == len(t.leaf_first) - 1
     assert v["n_groups"] == len(t.group_first) - 1
     np.testing.assert_array_equal(v["keys"].cpu().numpy().astype(np.uint64), t.keys)
@@ -105,7 +106,11 @@ def test_pair_list_matches_box_relation(gpu_lib, clustered, L, rcut, level_bits)
     gc, _ = _snapped(*t.group_boxes())
     off = pv["group_off"].cpu().numpy()
     ent = pv["entries"].cpu().numpy()
-    leaf = ent[:, 3].view(np.int32)
+    first = ent[:, 3].view(np.int32)
+    leaf = np.searchsorted(t.leaf_first, first)
+    np.testing.assert_array_equal(t.leaf_first[leaf], first)
+    np.testing.assert_array_equal(pv["counts"].cpu().numpy().astype(np.int64) + 1,
+                                  t.leaf_first[leaf + 1] - t.leaf_first[leaf])
     got = set()
     for g in range(len(off) - 1):
         for e in range(off[g], off[g + 1]):
