@@ -41,13 +41,14 @@ sys.path.insert(0, ROOT)
 METRIC = "PP interactions/sec and % of GB300 FP32 peak; learned-g vs exact-g speedup at error"
 UNIT = "interactions/s"
 
-# FP32 operations per evaluated pair in k_pp_exact (counted from the source,
-# FADD/FMUL = 1 flop, FFMA = 2, SFU rsqrt/sqrt/ex2 = 0, Kahan adds and the
-# cutoff select not counted): d 3 FADD; r^2 1 FMUL + 2 FFMA; r^2+eps^2 1 FADD;
-# Newton-corrected (r^2+eps^2)^-3/2 3 FMUL + 2 FFMA; r^2 c_v 1 FMUL; t 1 FADD;
-# degree-10 Horner 10 FFMA; ex2 argument 1 FMUL; f 1 FMUL; w 2 FMUL;
-# accumulation 3 FFMA  ->  5 FADD + 9 FMUL + 17 FFMA = 48 flop.
-FLOPS_PER_INTERACTION = 48
+# FP32 operations per evaluated pair in the exact PP kernel (counted from the
+# source, FADD/FMUL = 1 flop, FFMA = 2, SFU rsqrt/sqrt/ex2 = 0, Kahan adds and
+# the cutoff select not counted): d 3 FADD; r^2 1 FMUL + 2 FFMA; scaled
+# r^2 s2 + eps2s 1 FFMA; its cube 2 FMUL (one SFU rsqrt then gives the
+# inverse cube); r^2 c_v 1 FMUL; t 1 FADD; degree-10 Horner 10 FFMA; ex2
+# argument 1 FMUL; f 1 FMUL; w 2 FMUL; accumulation 3 FFMA
+#   ->  4 FADD + 8 FMUL + 16 FFMA = 44 flop.
+FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic per PP launch (bytes) from the ncu capture summarised in
 # profiles/pp_exact_zeldovich64.md, or None when the kernel changed since.
@@ -400,7 +401,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = computed * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": PP_TRAFFIC_BYTES,
-            "kernel": "k_pp_exact", "flops_per_interaction": FLOPS_PER_INTERACTION,
+            "kernel": "k_pp (exact factor)", "flops_per_interaction": FLOPS_PER_INTERACTION,
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
     if clk and clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (peak * clk["sm_mhz"] / sm_max)

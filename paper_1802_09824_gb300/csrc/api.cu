@@ -226,9 +226,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         bx.nside = 1 << bx.g;
         bx.S = std::ldexp(1.0, h->key_bits) / p.L;
         bx.h = p.L / bx.nside;
-        bx.G = (float)p.G;
-        double e2 = p.eps * p.eps;
-        bx.eps2 = (float)(e2 > 1e-24 ? e2 : 1e-24);
+        set_softening(bx, p.G, p.eps, p.rcut);
         bx.rcut2 = (float)(p.rcut * p.rcut);
         double rf = p.rcut * (1.0 + 3e-5);
         bx.rfilt2 = (float)(rf * rf);

@@ -140,9 +140,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     bx.nside = nside;
     bx.S = std::ldexp(1.0, T) / p.L;
     bx.h = p.L / nside;
-    bx.G = (float)p.G;
-    const double e2 = p.eps * p.eps;
-    bx.eps2 = (float)(e2 > 1e-24 ? e2 : 1e-24);
+    set_softening(bx, p.G, p.eps, p.rcut);
     bx.rcut2 = (float)(p.rcut * p.rcut);
     const double rf = p.rcut * (1.0 + 3e-5);
     bx.rfilt2 = (float)(rf * rf);

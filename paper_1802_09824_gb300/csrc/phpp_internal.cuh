@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 
 #include "../../include/phpp.h"
@@ -39,7 +41,27 @@ struct BoxDev {
     int32_t group_size;
     int32_t pad;
     float poly[kMaxPoly + 1];   // h(t) = sum poly[k] t^k, f = 2^(r^2 c_e) h
+    // Scaled softening for the exact kernel: x = r^2 s2 + eps2s is O(1) at the
+    // cutoff (s2 = 4^-k, a power of four near 1 / (rcut^2 + eps^2)), so x^3
+    // stays a normal FP32 number and (r^2 + eps^2)^(-3/2) = s2^(3/2) x^(-3/2)
+    // with the power of two s2^(3/2) folded into c_g = G s2^(3/2).
+    float s2;
+    float eps2s;       // max(eps^2 s2, 1e-12)
+    float c_g;
 };
+
+// Softening and force-scale constants of one box (see BoxDev).
+inline void set_softening(BoxDev &bx, double G, double eps, double rcut)
+{
+    const double e2 = eps * eps;
+    bx.G = (float)G;
+    bx.eps2 = (float)(e2 > 1e-24 ? e2 : 1e-24);
+    const int k = (int)std::lround(0.5 * std::log2(rcut * rcut + e2));
+    bx.s2 = (float)std::ldexp(1.0, -2 * k);
+    const double es = e2 * std::ldexp(1.0, -2 * k);
+    bx.eps2s = (float)(es > 1e-12 ? es : 1e-12);
+    bx.c_g = (float)(G * std::ldexp(1.0, -3 * k));
+}
 
 // Device-side status word bits.
 enum : uint32_t {

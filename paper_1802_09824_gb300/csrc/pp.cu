@@ -33,7 +33,7 @@ typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pai
 // Constants of one box, each duplicated into both halves of a pair.
 struct PairConsts {
     f2_t poly[kMaxPoly + 1];
-    f2_t eps2, c_v, c_e, m15, c15, m1;
+    f2_t s2, eps2s, c_v, c_e, m1;
     float rcut2, rfilt2;
 };
 
@@ -128,14 +128,12 @@ __device__ __forceinline__ void interact2(const float4 a, const float4 b, const 
     f2_t r2 = mul2(dx, dx);
     r2 = fma2(dy, dy, r2);
     r2 = fma2(dz, dz, r2);
-    // (r2 + eps2)^(-3/2): SFU rsqrt y, then the first-order Newton
-    // correction y^3 (1 + 3/2 (1 - x y^2)), which removes the SFU error
-    const f2_t x = add2(r2, c.eps2);
-    const f2_t y = pk(rsqrt_sfu(lo_of(x)), rsqrt_sfu(hi_of(x)));
-    const f2_t y2 = mul2(y, y);
-    const f2_t y3 = mul2(y2, y);
-    const f2_t e15 = fma2(mul2(x, c.m15), y2, c.c15);
-    const f2_t inv3 = fma2(y3, e15, y3);
+    // (r^2 + eps^2)^(-3/2) up to the box's power-of-two scale: one SFU
+    // rsqrt of x^3 with x = r^2 s2 + eps2s = O(1), so the SFU's relative
+    // error enters once (not tripled, as it would be in rsqrt(x)^3)
+    const f2_t x = fma2(r2, c.s2, c.eps2s);
+    const f2_t x3 = mul2(mul2(x, x), x);
+    const f2_t inv3 = pk(rsqrt_sfu(lo_of(x3)), rsqrt_sfu(hi_of(x3)));
     const f2_t sv = mul2(r2, c.c_v);
     const f2_t t = add2(pk(sqrt_sfu(lo_of(sv)), sqrt_sfu(hi_of(sv))), c.m1);
     f2_t h = c.poly[NPOLY];
@@ -158,7 +156,14 @@ __device__ __forceinline__ void interact2(const float4 a, const float4 b, const 
 // sources to a whole number of pairs per slot.  Plain FP32 partial sums over
 // runs of kRun pairs, each run added to the lane's total with Kahan
 // compensation.
-constexpr int kRun = 8;
+#ifndef PHPP_PP_RUN
+#define PHPP_PP_RUN 8
+#endif
+#ifndef PHPP_PP_UNROLL
+#define PHPP_PP_UNROLL 8
+#endif
+constexpr int kRun = PHPP_PP_RUN;
+constexpr int kUnroll = PHPP_PP_UNROLL;
 
 template <int NPOLY, int kSplit>
 __device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int npair, int h, const f2_t xi,
@@ -168,7 +173,7 @@ __device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int
     int s = 0;
     for (; s + kRun <= nstep; s += kRun) {
         f2_t px = 0ull, py = 0ull, pz = 0ull;
-#pragma unroll 4
+#pragma unroll kUnroll
         for (int u = 0; u < kRun; u++) {
             const int m = (s + u) * kSplit + h;
             interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
@@ -326,11 +331,10 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         if (!kUniform) {
 #pragma unroll
             for (int q = 0; q <= NPOLY; q++) cl.poly[q] = pk(bx.poly[q], bx.poly[q]);
-            cl.eps2 = pk(bx.eps2, bx.eps2);
+            cl.s2 = pk(bx.s2, bx.s2);
+            cl.eps2s = pk(bx.eps2s, bx.eps2s);
             cl.c_v = pk(bx.c_v, bx.c_v);
             cl.c_e = pk(bx.c_e, bx.c_e);
-            cl.m15 = pk(-1.5f, -1.5f);
-            cl.c15 = pk(1.5f, 1.5f);
             cl.m1 = pk(-1.f, -1.f);
             cl.rcut2 = bx.rcut2;
             cl.rfilt2 = bx.rfilt2;
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         }
         if (hs == 0 && ti < ni) {
             const int64_t o = a.perm[i0 + ti];
-            const float Gc = bx.G;
+            const float Gc = kLearned ? bx.G : bx.c_g;
             a.acc[3 * o + 0] = Gc * tx;
             a.acc[3 * o + 1] = Gc * ty;
             a.acc[3 * o + 2] = Gc * tz;
@@ -555,7 +559,7 @@ static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
     const BoxDev &b0 = lv->boxes_host[0];
     for (int b = 1; b < lv->n_boxes; b++) {
         const BoxDev &bx = lv->boxes_host[b];
-        if (memcmp(bx.poly, b0.poly, sizeof b0.poly) || bx.eps2 != b0.eps2 || bx.c_v != b0.c_v ||
+        if (memcmp(bx.poly, b0.poly, sizeof b0.poly) || bx.s2 != b0.s2 || bx.eps2s != b0.eps2s || bx.c_v != b0.c_v ||
             bx.c_e != b0.c_e || bx.rcut2 != b0.rcut2 || bx.rfilt2 != b0.rfilt2)
             return false;
     }
@@ -567,11 +571,10 @@ static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
         return (f2_t)u;
     };
     for (int q = 0; q <= kMaxPoly; q++) uc.poly[q] = dup(b0.poly[q]);
-    uc.eps2 = dup(b0.eps2);
+    uc.s2 = dup(b0.s2);
+    uc.eps2s = dup(b0.eps2s);
     uc.c_v = dup(b0.c_v);
     uc.c_e = dup(b0.c_e);
-    uc.m15 = dup(-1.5f);
-    uc.c15 = dup(1.5f);
     uc.m1 = dup(-1.f);
     uc.rcut2 = b0.rcut2;
     uc.rfilt2 = b0.rfilt2;
