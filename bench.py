@@ -45,9 +45,9 @@ UNIT = "interactions/s"
 # source, FADD/FMUL = 1 flop, FFMA = 2, SFU rsqrt/sqrt/ex2 = 0, Kahan adds and
 # the cutoff select not counted): d 3 FADD; r^2 1 FMUL + 2 FFMA; scaled
 # r^2 s2 + eps2s 1 FFMA; its cube 2 FMUL (one SFU rsqrt then gives the
-# inverse cube); r^2 c_v 1 FMUL; t 1 FADD; degree-10 Horner 10 FFMA; ex2
-# argument 1 FMUL; f 1 FMUL; w 2 FMUL; accumulation 3 FFMA
-#   ->  4 FADD + 8 FMUL + 16 FFMA = 44 flop.
+# inverse cube); t = sqrt(r^2) 2/rcut - 1 1 FFMA; degree-10 Horner 10 FFMA;
+# ex2 argument 1 FMUL; f 1 FMUL; w 2 FMUL; accumulation 3 FFMA
+#   ->  3 FADD + 7 FMUL + 17 FFMA = 44 flop.
 FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic per PP launch (bytes) from the ncu capture summarised in

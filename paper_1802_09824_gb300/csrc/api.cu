@@ -231,6 +231,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         double rf = p.rcut * (1.0 + 3e-5);
         bx.rfilt2 = (float)(rf * rf);
         bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
+        bx.c_t = (float)(2.0 / p.rcut);
         bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
         const int64_t nbx = box_offsets[b + 1] - box_offsets[b];
         bx.mass_default = nbx > 0 ? (float)(1.0 / (double)nbx) : 0.f;

@@ -145,6 +145,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     const double rf = p.rcut * (1.0 + 3e-5);
     bx.rfilt2 = (float)(rf * rf);
     bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
+    bx.c_t = (float)(2.0 / p.rcut);
     bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
     bx.mass_default = (float)(1.0 / (double)n);
     bx.cell_base = 0;

@@ -30,6 +30,7 @@ struct BoxDev {
     float rcut2;       // rcut^2 (cutoff decision of the PP kernel)
     float rfilt2;      // (rcut (1 + margin))^2 for conservative box tests
     float c_v;         // v = sqrt(r^2 c_v) = r / (R_s U), t = v - 1 in [-1, 1]
+    float c_t;         // 2 / rcut: t = sqrt(r^2) c_t - 1 (exact kernel)
     float c_e;         // exp(-r^2 / 4R_s^2) = 2^(r^2 c_e)
     float mass_default;
     int32_t g;         // ground level, N_side = 2^g

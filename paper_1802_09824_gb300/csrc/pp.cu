@@ -24,8 +24,22 @@
 namespace phpp {
 namespace {
 
-constexpr int kPPWarps = 8;
+#ifndef PHPP_PP_WARPS
+#define PHPP_PP_WARPS 8
+#endif
+#ifndef PHPP_PP_BLOCKS0
+#define PHPP_PP_BLOCKS0 2
+#endif
+#ifndef PHPP_PP_BLOCKS1
+#define PHPP_PP_BLOCKS1 3
+#endif
+constexpr int kPPWarps = PHPP_PP_WARPS;
 constexpr int kPPThreads = kPPWarps * 32;
+// resident blocks per SM of the two kernel shapes (pp_variant 0 and 1): the
+// register budget each instantiation is compiled for, and the persistent
+// grid (SMs x blocks)
+constexpr int kBlocks0 = PHPP_PP_BLOCKS0;
+constexpr int kBlocks1 = PHPP_PP_BLOCKS1;
 constexpr int kJBuf = 256;      // staged sources per warp (even)
 
 typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pair
@@ -33,7 +47,7 @@ typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pai
 // Constants of one box, each duplicated into both halves of a pair.
 struct PairConsts {
     f2_t poly[kMaxPoly + 1];
-    f2_t s2, eps2s, c_v, c_e, m1;
+    f2_t s2, eps2s, c_t, c_e, m1;
     float rcut2, rfilt2;
 };
 
@@ -134,8 +148,7 @@ __device__ __forceinline__ void interact2(const float4 a, const float4 b, const 
     const f2_t x = fma2(r2, c.s2, c.eps2s);
     const f2_t x3 = mul2(mul2(x, x), x);
     const f2_t inv3 = pk(rsqrt_sfu(lo_of(x3)), rsqrt_sfu(hi_of(x3)));
-    const f2_t sv = mul2(r2, c.c_v);
-    const f2_t t = add2(pk(sqrt_sfu(lo_of(sv)), sqrt_sfu(hi_of(sv))), c.m1);
+    const f2_t t = fma2(pk(sqrt_sfu(lo_of(r2)), sqrt_sfu(hi_of(r2))), c.c_t, c.m1);   // 2 r / rcut - 1
     f2_t h = c.poly[NPOLY];
 #pragma unroll
     for (int q = NPOLY - 1; q >= 0; q--) h = fma2(h, t, c.poly[q]);
@@ -252,10 +265,12 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 }
 
 // 32 consecutive pair entries, one per lane, with the exclusive prefix sums
-// of their leaf sizes.
+// of their leaf sizes: concatenated particle q of the batch lies in the
+// entry whose range [excl, excl + count) holds q, at row base + q of the
+// leaf-relative positions (base = first particle - excl).
 struct EntryBatch {
     float4 ent;
-    int l0, excl, total;
+    int base, excl, total;
     __device__ __forceinline__ void load(const PPArgs &a, int64_t eb, int64_t e1, int lane)
     {
         const int64_t e = eb + lane;
@@ -265,29 +280,31 @@ struct EntryBatch {
             ent = a.entries[e];
             cnt = (int)a.ecount[e] + 1;
         }
-        l0 = __float_as_int(ent.w);
         const int incl = warp_incl_scan_i(cnt, lane);
         excl = incl - cnt;
+        base = __float_as_int(ent.w) - excl;
         total = __shfl_sync(0xffffffffu, incl, 31);
     }
 };
 
 // One staging round: the particle each lane loads (in flight until used) and
-// the offset of its entry.
+// the offset of its entry.  The entry of lane t's particle q = q0 + t is
+// found without a search: the entries starting inside [q0, q0 + 32) set
+// their start bit in a warp-wide OR, so the owner is the number of entries
+// started before q0 (`before`, carried from round to round) plus the start
+// bits at or below t, minus one.
 struct Round {
     float4 p;
     float ox, oy, oz;
     bool valid;
-    __device__ __forceinline__ void issue(const PPArgs &a, const EntryBatch &b, int q0, int lane)
+    __device__ __forceinline__ void issue(const PPArgs &a, const EntryBatch &b, int q0, int lane, int &before)
     {
         const int q = q0 + lane;
-        int o = 0;   // the lane whose entry holds concatenated particle q
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int ex = __shfl_sync(0xffffffffu, b.excl, o + step);
-            if (ex <= q) o += step;
-        }
-        const int j = __shfl_sync(0xffffffffu, b.l0, o) + (q - __shfl_sync(0xffffffffu, b.excl, o));
+        const unsigned s = (unsigned)(b.excl - q0);
+        const unsigned starts = __reduce_or_sync(0xffffffffu, s < 32u ? 1u << s : 0u);
+        const int o = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        before += __popc(starts);
+        const int j = __shfl_sync(0xffffffffu, b.base, o) + q;
         ox = __shfl_sync(0xffffffffu, b.ent.x, o);
         oy = __shfl_sync(0xffffffffu, b.ent.y, o);
         oz = __shfl_sync(0xffffffffu, b.ent.z, o);
@@ -333,7 +350,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
             for (int q = 0; q <= NPOLY; q++) cl.poly[q] = pk(bx.poly[q], bx.poly[q]);
             cl.s2 = pk(bx.s2, bx.s2);
             cl.eps2s = pk(bx.eps2s, bx.eps2s);
-            cl.c_v = pk(bx.c_v, bx.c_v);
+            cl.c_t = pk(bx.c_t, bx.c_t);
             cl.c_e = pk(bx.c_e, bx.c_e);
             cl.m1 = pk(-1.f, -1.f);
             cl.rcut2 = bx.rcut2;
@@ -354,9 +371,10 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         for (int64_t eb = a.group_off[g]; eb < e1; eb += 32) {
             EntryBatch bt;
             bt.load(a, eb, e1, lane);
+            int before = 0;
             for (int q0 = 0; q0 < bt.total; q0 += 32) {
                 Round cur;
-                cur.issue(a, bt, q0, lane);
+                cur.issue(a, bt, q0, lane, before);
                 float4 p = cur.p;
                 bool keep = false;
                 if (cur.valid) {
@@ -543,10 +561,10 @@ int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_
     a.mlp_w = mlp_w;
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
-    const int grid = sm_count() * 2;
-    if (lv->group_size == 8) k_pp<10, true, 2, 4, false><<<grid, kPPThreads, 0, s>>>(a);
-    else if (lv->group_size == 16) k_pp<10, true, 2, 2, false><<<grid, kPPThreads, 0, s>>>(a);
-    else k_pp<10, true, 2, 1, false><<<grid, kPPThreads, 0, s>>>(a);
+    const int grid = sm_count() * kBlocks0;
+    if (lv->group_size == 8) k_pp<10, true, kBlocks0, 4, false><<<grid, kPPThreads, 0, s>>>(a);
+    else if (lv->group_size == 16) k_pp<10, true, kBlocks0, 2, false><<<grid, kPPThreads, 0, s>>>(a);
+    else k_pp<10, true, kBlocks0, 1, false><<<grid, kPPThreads, 0, s>>>(a);
     count_launch();
     return cuda_check(cudaGetLastError(), "learned pp kernel");
 }
@@ -559,7 +577,7 @@ static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
     const BoxDev &b0 = lv->boxes_host[0];
     for (int b = 1; b < lv->n_boxes; b++) {
         const BoxDev &bx = lv->boxes_host[b];
-        if (memcmp(bx.poly, b0.poly, sizeof b0.poly) || bx.s2 != b0.s2 || bx.eps2s != b0.eps2s || bx.c_v != b0.c_v ||
+        if (memcmp(bx.poly, b0.poly, sizeof b0.poly) || bx.s2 != b0.s2 || bx.eps2s != b0.eps2s || bx.c_t != b0.c_t ||
             bx.c_e != b0.c_e || bx.rcut2 != b0.rcut2 || bx.rfilt2 != b0.rfilt2)
             return false;
     }
@@ -573,7 +591,7 @@ static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
     for (int q = 0; q <= kMaxPoly; q++) uc.poly[q] = dup(b0.poly[q]);
     uc.s2 = dup(b0.s2);
     uc.eps2s = dup(b0.eps2s);
-    uc.c_v = dup(b0.c_v);
+    uc.c_t = dup(b0.c_t);
     uc.c_e = dup(b0.c_e);
     uc.m1 = dup(-1.f);
     uc.rcut2 = b0.rcut2;
@@ -593,24 +611,24 @@ int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaS
         return fail(PH_ERR_STATE, "unsupported polynomial degree %d", npoly);
     const bool uni = uniform_consts(lv, a.uc);
     const bool three = lv->pp_variant == 1;
-    const int grid = sm_count() * (three ? 3 : 2);
+    const int grid = sm_count() * (three ? kBlocks1 : kBlocks0);
     const int gs = lv->group_size;
     if (uni) {
         if (three) {
-            if (gs == 8) launch_pp<false, 3, 4, true>(npoly, grid, s, a);
-            else if (gs == 16) launch_pp<false, 3, 2, true>(npoly, grid, s, a);
-            else launch_pp<false, 3, 1, true>(npoly, grid, s, a);
+            if (gs == 8) launch_pp<false, kBlocks1, 4, true>(npoly, grid, s, a);
+            else if (gs == 16) launch_pp<false, kBlocks1, 2, true>(npoly, grid, s, a);
+            else launch_pp<false, kBlocks1, 1, true>(npoly, grid, s, a);
         } else {
-            if (gs == 8) launch_pp<false, 2, 4, true>(npoly, grid, s, a);
-            else if (gs == 16) launch_pp<false, 2, 2, true>(npoly, grid, s, a);
-            else launch_pp<false, 2, 1, true>(npoly, grid, s, a);
+            if (gs == 8) launch_pp<false, kBlocks0, 4, true>(npoly, grid, s, a);
+            else if (gs == 16) launch_pp<false, kBlocks0, 2, true>(npoly, grid, s, a);
+            else launch_pp<false, kBlocks0, 1, true>(npoly, grid, s, a);
         }
     } else {
         // boxes with different constants: the two-block shape only
-        const int g2 = sm_count() * 2;
-        if (gs == 8) launch_pp<false, 2, 4, false>(npoly, g2, s, a);
-        else if (gs == 16) launch_pp<false, 2, 2, false>(npoly, g2, s, a);
-        else launch_pp<false, 2, 1, false>(npoly, g2, s, a);
+        const int g2 = sm_count() * kBlocks0;
+        if (gs == 8) launch_pp<false, kBlocks0, 4, false>(npoly, g2, s, a);
+        else if (gs == 16) launch_pp<false, kBlocks0, 2, false>(npoly, g2, s, a);
+        else launch_pp<false, kBlocks0, 1, false>(npoly, g2, s, a);
     }
     count_launch();
     return cuda_check(cudaGetLastError(), "pp kernel");
