@@ -139,7 +139,7 @@ static void free_leaves(ph_leaves *h)
     DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
                       &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
                       &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
-                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->group_cell, &h->group_box,
+                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->group_cell, &h->group_box,
                       &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
     for (DevBuf *b : bufs) release(*b);
 }
@@ -270,6 +270,8 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     ENS(h->group_ref, 24 * N);
     ENS(h->group_c4, 16 * N);
     ENS(h->group_h4, 16 * N);
+    ENS(h->leaf_r4, 16 * N);
+    ENS(h->group_r4, 16 * N);
     ENS(h->group_cell, 4 * N);
     ENS(h->group_box, 4 * N);
     ENS(h->pos_leaf, 16 * N);

@@ -283,39 +283,71 @@ __device__ __forceinline__ double dkey_inv(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
-// Bounding box of each leaf (or group), one thread per box: FP64 reference
-// point near the box centre, FP32 half extents around it rounded up, FP32
-// reference point relative to the ground cell's lower corner.
+// Bounding box of each leaf (or group): FP64 reference point near the box
+// centre, FP32 half extents around it rounded up, FP32 reference point
+// relative to the ground cell's lower corner.  A warp takes 32 consecutive
+// boxes: for each, the lanes stride over its particles and combine their
+// min/max, and lane j keeps box j's bounds; then every lane finishes its own
+// box (so the FP64 arithmetic runs 32 boxes per instruction).
 //
 // The reference point is the centre rounded to a multiple of U = 2^(e-24),
 // the FP32 spacing of the box's largest |coordinate| (2^(e-1) <= m < 2^e),
 // so that an FP32 coordinate minus it is exact; rounding to a multiple of U
-// is done as (c + 1.5 2^52 U) - 1.5 2^52 U (round half to even).
+// is done as (c + 1.5 2^52 U) - 1.5 2^52 U (round half to even).  Being a
+// multiple of U below 2^e in magnitude, it is itself an FP32 number: r4
+// holds that exact FP32 copy.
 __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const double *xw, const uint64_t *keys,
-                        const BoxDev *boxes, int T, double *ref, float4 *c4, float4 *h4, int32_t *cell_of,
-                        int32_t *box_of)
+                        const BoxDev *boxes, int T, double *ref, float4 *r4, float4 *c4, float4 *h4,
+                        int32_t *cell_of, int32_t *box_of)
 {
     const int count = *scan_total;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
-        const int a = first[l], e = first[l + 1];
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int l0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; l0 < count; l0 += warps * 32) {
         long long lo[3], hi[3];
+        const int nbox = count - l0 < 32 ? count - l0 : 32;
+        for (int j = 0; j < nbox; j++) {
+            const int a = first[l0 + j], e = first[l0 + j + 1];
+            long long jl[3], jh[3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) lo[d] = hi[d] = dkey(xw[3 * (int64_t)a + d]);
-        for (int k = a + 1; k < e; k++) {
+            for (int d = 0; d < 3; d++) jl[d] = jh[d] = dkey(xw[3 * (int64_t)a + d]);
+            for (int k = a + 1 + lane; k < e; k += 32) {
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const long long v = dkey(xw[3 * (int64_t)k + d]);
-                lo[d] = v < lo[d] ? v : lo[d];
-                hi[d] = v > hi[d] ? v : hi[d];
+                for (int d = 0; d < 3; d++) {
+                    const long long v = dkey(xw[3 * (int64_t)k + d]);
+                    jl[d] = v < jl[d] ? v : jl[d];
+                    jh[d] = v > jh[d] ? v : jh[d];
+                }
+            }
+            if (e - a > 1) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        const long long vl = __shfl_xor_sync(0xffffffffu, jl[d], o);
+                        const long long vh = __shfl_xor_sync(0xffffffffu, jh[d], o);
+                        jl[d] = vl < jl[d] ? vl : jl[d];
+                        jh[d] = vh > jh[d] ? vh : jh[d];
+                    }
+                }
+            }
+            if (lane == j) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    lo[d] = jl[d];
+                    hi[d] = jh[d];
+                }
             }
         }
-        const uint64_t key = keys[a];
+        if (lane >= nbox) continue;
+        const int l = l0 + lane;
+        const uint64_t key = keys[first[l]];
         const int bi = 3 * T < 64 ? (int)(key >> (3 * T)) : 0;
         const BoxDev &bx = boxes[bi];
         const uint32_t ground = (uint32_t)((key >> (3 * bx.b)) & ((1ull << (3 * bx.g)) - 1ull));
         const uint32_t gz = ground % bx.nside, gy = (ground / bx.nside) % bx.nside, gx = ground / (bx.nside * bx.nside);
         const uint32_t gc[3] = {gx, gy, gz};
-        float c[3], hh[3];
+        float c[3], hh[3], rf[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double vlo = dkey_inv(lo[d]), vhi = dkey_inv(hi[d]);
@@ -326,9 +358,11 @@ __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const d
             const double r = __dsub_rn(__dadd_rn(cen, C), C);
             const double half = fmax(__dsub_rn(vhi, r), __dsub_rn(r, vlo));
             ref[3 * (int64_t)l + d] = r;
+            rf[d] = __double2float_rn(r);   // exact
             c[d] = __double2float_rn(__dsub_rn(r, __dmul_rn((double)gc[d], bx.h)));
             hh[d] = __double2float_ru(half);
         }
+        r4[l] = make_float4(rf[0], rf[1], rf[2], 0.f);
         c4[l] = make_float4(c[0], c[1], c[2], 0.f);
         h4[l] = make_float4(hh[0], hh[1], hh[2], 0.f);
         if (cell_of) cell_of[l] = bx.cell_base + (int)ground;
@@ -337,19 +371,21 @@ __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const d
 }
 
 __global__ void k_pos(int64_t n, const double *xw, const float *mass_sorted, const int32_t *leaf_scan,
-                      const int32_t *group_scan, const double *leaf_ref, const double *group_ref, float4 *pos_leaf,
-                      float4 *pos_group)
+                      const int32_t *group_scan, const double *leaf_ref, const float4 *leaf_r4, const float4 *group_r4,
+                      float4 *pos_leaf, float4 *pos_group)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = leaf_scan[k + 1] - 1;
         const int64_t g = group_scan[k + 1] - 1;
+        const float4 lr4 = leaf_r4[l], gr4 = group_r4[g];
+        const float lrf[3] = {lr4.x, lr4.y, lr4.z}, grf[3] = {gr4.x, gr4.y, gr4.z};
         float p[3], q[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double lr = leaf_ref[3 * l + d];
-            p[d] = __double2float_rn(__dsub_rn(xw[3 * k + d], lr));
-            // same FP64 offset and FP32 add as the PP kernel's source shift
-            const float off = __double2float_rn(__dsub_rn(lr, group_ref[3 * g + d]));
+            p[d] = __double2float_rn(__dsub_rn(xw[3 * k + d], leaf_ref[3 * l + d]));
+            // the same FP32 offset (the rounded difference of the two exact FP32
+            // reference points) and FP32 add as the PP kernel's source shift
+            const float off = __fsub_rn(lrf[d], grf[d]);
             q[d] = __fadd_rn(p[d], off);
         }
         const float m = mass_sorted[k];
@@ -469,19 +505,21 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
         cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
         cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
     }
-    const int box_grid = grid_for(n);
+    const int box_grid = sm_count() * 16;   // one warp per box, grid-stride
     k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
-                                          static_cast<float4 *>(h->leaf_c4.p), static_cast<float4 *>(h->leaf_h4.p),
-                                          nullptr, nullptr);
+                                          static_cast<float4 *>(h->leaf_r4.p), static_cast<float4 *>(h->leaf_c4.p),
+                                          static_cast<float4 *>(h->leaf_h4.p), nullptr, nullptr);
     count_launch();
     k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, xw, sk, boxes, T,
-                                          static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_c4.p),
-                                          static_cast<float4 *>(h->group_h4.p), static_cast<int32_t *>(h->group_cell.p),
+                                          static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_r4.p),
+                                          static_cast<float4 *>(h->group_c4.p), static_cast<float4 *>(h->group_h4.p),
+                                          static_cast<int32_t *>(h->group_cell.p),
                                           static_cast<int32_t *>(h->group_box.p));
     count_launch();
     if (n > 0)
         k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
-                                               static_cast<const double *>(h->group_ref.p),
+                                               static_cast<const float4 *>(h->leaf_r4.p),
+                                               static_cast<const float4 *>(h->group_r4.p),
                                                static_cast<float4 *>(h->pos_leaf.p),
                                                static_cast<float4 *>(h->pos_group.p));
         count_launch();

@@ -37,6 +37,7 @@ struct ph_leaves {
     phpp::DevBuf leaf_c4, leaf_h4;        // float4[n] (centre in cell frame, half extents)
     phpp::DevBuf group_ref;      // double[3 n]
     phpp::DevBuf group_c4, group_h4;      // float4[n]
+    phpp::DevBuf leaf_r4, group_r4;       // float4[n]: the reference points in FP32 (exact; see k_boxes)
     phpp::DevBuf group_cell;     // int32[n] global ground cell of each group
     phpp::DevBuf group_box;      // int32[n]
     phpp::DevBuf pos_leaf;       // float4[n]

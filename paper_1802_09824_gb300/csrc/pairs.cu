@@ -10,8 +10,10 @@
 // images; at most one of them can be within R_cut < L/2 of any particle).
 //
 // The test runs in FP32 on cell-relative centres with a relative margin on
-// R_cut, so no pair the PP kernel could accept is ever dropped; the stored
-// offset of an accepted pair is computed from the FP64 reference points.
+// R_cut, so no pair the PP kernel could accept is ever dropped.  The stored
+// offset of an accepted pair is the difference of the reference points
+// rounded once to FP32: in FP32 directly when no periodic image is involved
+// (the reference points are FP32 numbers), from the FP64 points otherwise.
 #include "handles.cuh"
 
 namespace phpp {
@@ -27,6 +29,7 @@ struct PairArgs {
     const int32_t *cell_leaf_first;
     const float4 *leaf_c4, *leaf_h4;
     const double *leaf_ref;
+    const float4 *leaf_r4, *group_r4;   // the reference points as (exact) FP32
     int64_t *cnt;            // count pass output [n_groups]
     const int64_t *off;      // fill pass input   [n_groups + 1]
     float4 *ent;             // fill pass output: offset x, y, z, first source particle (bits)
@@ -49,14 +52,17 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 // One warp per target group.  Lane t < 27 takes neighbour cell t (offset
 // (t/9-1, t/3%3-1, t%3-1)), skips it when the whole cell is beyond rcut of
 // the group's box, and contributes its leaf count; the warp then walks the
-// concatenated candidate leaves 32 at a time, each lane finding the
-// neighbour that owns its candidate by a binary search over the lanes'
-// exclusive prefix counts.  Candidates keep the order (neighbour, leaf), so
-// the list is deterministic.
+// concatenated candidate leaves 32 at a time.  The neighbour that owns a
+// candidate follows from the runs that start inside the current 32: their
+// start bits are OR-ed across the warp, and the owner of position q0 + t is
+// the number of runs started before q0 plus the start bits at or below t,
+// minus one (lanes with no leaves start no run).  Candidates keep the order
+// (neighbour, leaf), so the list is deterministic.
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ int2 s_run[kThreads / 32][32];   // per warp: (lane, first leaf - excl) of each run
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int ng = *a.n_groups;
@@ -89,31 +95,32 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
         const int incl = warp_incl_scan_i(cnt, lane);
         const int excl = incl - cnt;
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        double gref[3] = {0, 0, 0};
+        float4 gr4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int64_t base = 0;
         if (kFill) {
-            gref[0] = a.group_ref[3 * (int64_t)g];
-            gref[1] = a.group_ref[3 * (int64_t)g + 1];
-            gref[2] = a.group_ref[3 * (int64_t)g + 2];
+            gr4 = a.group_r4[g];
             base = a.off[g];
         }
+        // the lanes with leaves, in lane order, as runs (lane, first leaf - excl):
+        // candidate q of run k is leaf (first - excl) + q
+        const unsigned nonempty = __ballot_sync(0xffffffffu, cnt > 0);
+        if (cnt > 0) s_run[w][__popc(nonempty & lt)] = make_int2(lane, l0 - excl);
+        __syncwarp();
         int64_t count = 0;
+        int before = 0;   // runs started before q0
         for (int q0 = 0; q0 < total; q0 += 32) {
             const int q = q0 + lane;
-            // owner: the largest lane o with excl_o <= q (counts are >= 0)
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int e = __shfl_sync(0xffffffffu, excl, o + step);
-                if (e <= q) o += step;
-            }
-            const int lo0 = __shfl_sync(0xffffffffu, l0, o);
-            const int eo = __shfl_sync(0xffffffffu, excl, o);
+            const unsigned sq = (unsigned)(excl - q0);
+            const unsigned starts = __reduce_or_sync(0xffffffffu, (cnt > 0 && sq < 32u) ? 1u << sq : 0u);
+            const int r = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;   // owner run
+            before += __popc(starts);
+            const int2 ru = s_run[w][r];
+            const int o = ru.x, lb = ru.y;
             bool acc = false;
             int l = 0;
             const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
             if (q < total) {
-                l = lo0 + (q - eo);
+                l = lb + q;
                 const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
                 const float px = fmaxf(fabsf((lc.x + odx * hc) - gc.x) - (gh.x + lh.x), 0.f);
                 const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
@@ -128,12 +135,23 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                     const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
                     const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
                     const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
-                    const double *lr = a.leaf_ref + 3 * (int64_t)l;
-                    const double L = bx.L;
                     float4 e;
-                    e.x = __double2float_rn((lr[0] + sx * L) - gref[0]);
-                    e.y = __double2float_rn((lr[1] + sy * L) - gref[1]);
-                    e.z = __double2float_rn((lr[2] + sz * L) - gref[2]);
+                    if ((sx | sy | sz) == 0) {
+                        // the rounded difference of two FP32 numbers, exactly the
+                        // shift the target frame was built with (pos_group)
+                        const float4 lr4 = a.leaf_r4[l];
+                        e.x = __fsub_rn(lr4.x, gr4.x);
+                        e.y = __fsub_rn(lr4.y, gr4.y);
+                        e.z = __fsub_rn(lr4.z, gr4.z);
+                    } else {
+                        // a periodic image: the FP64 difference rounded once
+                        const double *lr = a.leaf_ref + 3 * (int64_t)l;
+                        const double *gr = a.group_ref + 3 * (int64_t)g;
+                        const double L = bx.L;
+                        e.x = __double2float_rn((lr[0] + sx * L) - gr[0]);
+                        e.y = __double2float_rn((lr[1] + sy * L) - gr[1]);
+                        e.z = __double2float_rn((lr[2] + sz * L) - gr[2]);
+                    }
                     const int f0 = a.leaf_first[l];
                     e.w = __int_as_float(f0);
                     a.ent[pos] = e;
@@ -145,6 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             count += __popc(bal);
         }
         if (!kFill && lane == 0) a.cnt[g] = count;
+        __syncwarp();   // s_run is rewritten for the next group
     }
 }
 
@@ -164,6 +183,8 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.leaf_c4 = static_cast<const float4 *>(lv->leaf_c4.p);
     a.leaf_h4 = static_cast<const float4 *>(lv->leaf_h4.p);
     a.leaf_ref = static_cast<const double *>(lv->leaf_ref.p);
+    a.leaf_r4 = static_cast<const float4 *>(lv->leaf_r4.p);
+    a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);
     a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
     a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
     a.off = static_cast<const int64_t *>(pr->group_off.p);

@@ -51,6 +51,19 @@ struct BoxDev {
     float c_g;
 };
 
+// Streaming multiprocessors of the current device (persistent grids).
+inline int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
 // Softening and force-scale constants of one box (see BoxDev).
 inline void set_softening(BoxDev &bx, double G, double eps, double rcut)
 {

@@ -494,18 +494,6 @@ __global__ void __launch_bounds__(kPPThreads) k_count_within(PPArgs a)
     if (cnt_within) atomicAdd(a.n_inter, cnt_within);
 }
 
-int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 }  // namespace
 
 static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArgs &a);
