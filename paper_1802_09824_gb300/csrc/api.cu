@@ -139,7 +139,7 @@ static void free_leaves(ph_leaves *h)
     DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
                       &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
                       &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
-                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->group_cell, &h->group_box,
+                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->group_cell, &h->group_box,
                       &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
     for (DevBuf *b : bufs) release(*b);
 }
@@ -221,6 +221,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         BoxDev &bx = h->boxes_host[b];
         memset(&bx, 0, sizeof bx);
         bx.L = p.L;
+        bx.L_up = float_at_or_above(p.L);
         bx.g = ground_level(p.L, p.rcut);
         bx.b = h->key_bits - bx.g;
         bx.nside = 1 << bx.g;
@@ -272,6 +273,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     ENS(h->group_h4, 16 * N);
     ENS(h->leaf_r4, 16 * N);
     ENS(h->group_r4, 16 * N);
+    ENS(h->box_ext, 48 * N);
     ENS(h->group_cell, 4 * N);
     ENS(h->group_box, 4 * N);
     ENS(h->pos_leaf, 16 * N);

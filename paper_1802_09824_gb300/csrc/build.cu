@@ -22,6 +22,7 @@
 // group, derived from the first by one FP32 add of the FP64-computed offset,
 // exactly as the PP kernel shifts source particles, so that a particle seen
 // as target and as source has bitwise the same coordinates.
+#include <climits>
 #include <cmath>
 
 #include "handles.cuh"
@@ -51,11 +52,19 @@ __device__ __forceinline__ double wrap_coord(double x, double L)
 
 __device__ __forceinline__ uint32_t quant_coord(double xw, double S, int T)
 {
-    double q = floor(__dmul_rn(xw, S));
-    double top = (double)((1u << T) - 1u);
-    if (!(q >= 0.0)) q = 0.0;
-    if (q > top) q = top;
-    return (uint32_t)q;
+    // floor(xw S) of a wrapped (finite, non-negative) coordinate, clamped
+    const int q = __double2int_rd(__dmul_rn(xw, S));
+    const int top = (1 << T) - 1;
+    return (uint32_t)(q < 0 ? 0 : (q > top ? top : q));
+}
+
+// Wrapped coordinate of an FP32 input: the in-box test runs in FP32 (x < L
+// exactly when x < L_up), so only the multiply of the key and the widening
+// to FP64 remain on the FP64 pipe for particles already in the box.
+__device__ __forceinline__ double wrap_f32(float x, const BoxDev &bx)
+{
+    if (x >= 0.f && x < bx.L_up) return (double)x;
+    return wrap_coord((double)x, bx.L);
 }
 
 // Spread the low 21 bits of v so that bit k lands on bit 3k.
@@ -107,32 +116,45 @@ __device__ __forceinline__ uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z,
     return interleave3(X[0], X[1], X[2]);
 }
 
-__device__ __forceinline__ void load_pos(const void *pos, int pos_type, int64_t i, double &x, double &y, double &z)
+// Particle i's coordinates wrapped into [0, L) in FP64 (non-finite input
+// counts as 0 and is reported once per particle through `bad`).
+template <int kPosType>
+__device__ __forceinline__ void wrapped_pos(const void *pos, int64_t i, const BoxDev &bx, double &x, double &y,
+                                            double &z, bool &bad)
 {
-    if (pos_type == PH_F64) {
+    if (kPosType == PH_F64) {
         const double *p = static_cast<const double *>(pos) + 3 * i;
         x = p[0]; y = p[1]; z = p[2];
+        bad = !(isfinite(x) && isfinite(y) && isfinite(z));
+        if (bad) x = y = z = 0.0;
+        x = wrap_coord(x, bx.L);
+        y = wrap_coord(y, bx.L);
+        z = wrap_coord(z, bx.L);
     } else {
         const float *p = static_cast<const float *>(pos) + 3 * i;
-        x = p[0]; y = p[1]; z = p[2];
+        float fx = p[0], fy = p[1], fz = p[2];
+        bad = !(isfinite(fx) && isfinite(fy) && isfinite(fz));
+        if (bad) fx = fy = fz = 0.f;
+        x = wrap_f32(fx, bx);
+        y = wrap_f32(fy, bx);
+        z = wrap_f32(fz, bx);
     }
 }
 
-__global__ void k_keys(const void *pos, int pos_type, int64_t n, const int32_t *box_first, int nb,
-                       const BoxDev *boxes, int T, int key_kind, uint64_t *keys, int32_t *vals, uint32_t *status)
+template <int kPosType>
+__global__ void k_keys(const void *pos, int64_t n, const int32_t *box_first, int nb, const BoxDev *boxes, int T,
+                       int key_kind, uint64_t *keys, int32_t *vals, uint32_t *status)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int bi = find_box(box_first, nb, i);
+        const int bi = nb > 1 ? find_box(box_first, nb, i) : 0;
         const BoxDev &bx = boxes[bi];
         double x, y, z;
-        load_pos(pos, pos_type, i, x, y, z);
-        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
-            atomicOr(status, ST_NONFINITE);
-            x = y = z = 0.0;
-        }
-        uint32_t qx = quant_coord(wrap_coord(x, bx.L), bx.S, T);
-        uint32_t qy = quant_coord(wrap_coord(y, bx.L), bx.S, T);
-        uint32_t qz = quant_coord(wrap_coord(z, bx.L), bx.S, T);
+        bool bad;
+        wrapped_pos<kPosType>(pos, i, bx, x, y, z, bad);
+        if (bad) atomicOr(status, ST_NONFINITE);
+        const uint32_t qx = quant_coord(x, bx.S, T);
+        const uint32_t qy = quant_coord(y, bx.S, T);
+        const uint32_t qz = quant_coord(z, bx.S, T);
         const int b = bx.b;
         const uint32_t lm = (1u << b) - 1u;
         uint64_t ground = ((uint64_t)(qx >> b) * bx.nside + (qy >> b)) * bx.nside + (qz >> b);
@@ -144,20 +166,20 @@ __global__ void k_keys(const void *pos, int pos_type, int64_t n, const int32_t *
     }
 }
 
-__global__ void k_gather(const void *pos, int pos_type, const float *mass, int64_t n, const uint64_t *keys,
-                         const int32_t *perm, const BoxDev *boxes, int T, double *xw, float *mass_sorted,
-                         uint32_t *status)
+template <int kPosType>
+__global__ void k_gather(const void *pos, const float *mass, int64_t n, const uint64_t *keys, const int32_t *perm,
+                         const BoxDev *boxes, int T, double *xw, float *mass_sorted, uint32_t *status)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[k];
         const int bi = 3 * T < 64 ? (int)(keys[k] >> (3 * T)) : 0;
         const BoxDev &bx = boxes[bi];
         double x, y, z;
-        load_pos(pos, pos_type, i, x, y, z);
-        if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = 0.0;
-        xw[3 * k + 0] = wrap_coord(x, bx.L);
-        xw[3 * k + 1] = wrap_coord(y, bx.L);
-        xw[3 * k + 2] = wrap_coord(z, bx.L);
+        bool bad;
+        wrapped_pos<kPosType>(pos, i, bx, x, y, z, bad);
+        xw[3 * k + 0] = x;
+        xw[3 * k + 1] = y;
+        xw[3 * k + 2] = z;
         float m = mass ? mass[i] : bx.mass_default;
         if (!isfinite(m)) {
             atomicOr(status, ST_NONFINITE);
@@ -263,10 +285,20 @@ __global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, in
     }
 }
 
-__global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, int32_t *first)
+// First particle of every leaf (or group); also resets the box's extent
+// accumulators (ordered-integer min and max per axis) for k_extents.
+__global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, int32_t *first, long long *ext)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        if (flag[k]) first[scan[k]] = (int32_t)k;
+        if (flag[k]) {
+            const int64_t l = scan[k];
+            first[l] = (int32_t)k;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                ext[6 * l + d] = LLONG_MAX;
+                ext[6 * l + 3 + d] = LLONG_MIN;
+            }
+        }
         if (k == n - 1) first[scan[n]] = (int32_t)n;
     }
 }
@@ -283,12 +315,53 @@ __device__ __forceinline__ double dkey_inv(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
-// Bounding box of each leaf (or group): FP64 reference point near the box
-// centre, FP32 half extents around it rounded up, FP32 reference point
-// relative to the ground cell's lower corner.  A warp takes 32 consecutive
-// boxes: for each, the lanes stride over its particles and combine their
-// min/max, and lane j keeps box j's bounds; then every lane finishes its own
-// box (so the FP64 arithmetic runs 32 boxes per instruction).
+// Per-axis extents of every leaf (or group), one thread per particle: the
+// particles of a box are consecutive, so a warp combines each box's part of
+// its 32 particles by a segmented reduction (shuffle down within runs of the
+// same box), and the first lane of each run folds that into the box's
+// accumulators with 64-bit atomic min/max (boxes may straddle warps).
+// Coordinates enter as ordered integers (dkey), so the integer order is the
+// FP64 order.
+__global__ void k_extents(const double *xw, int64_t n, const int32_t *scan, long long *ext)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (int64_t base = k0; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = base + lane;
+        const bool in = k < n;
+        const int l = in ? scan[k + 1] - 1 : -1;
+        long long lo[3], hi[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) lo[d] = hi[d] = in ? dkey(xw[3 * k + d]) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int lo_l = __shfl_down_sync(0xffffffffu, l, o);
+            const bool same = lane + o < 32 && lo_l == l;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const long long vl = __shfl_down_sync(0xffffffffu, lo[d], o);
+                const long long vh = __shfl_down_sync(0xffffffffu, hi[d], o);
+                if (same) {
+                    lo[d] = vl < lo[d] ? vl : lo[d];
+                    hi[d] = vh > hi[d] ? vh : hi[d];
+                }
+            }
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, l, 1);
+        if (in && (lane == 0 || prev != l)) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                atomicMin(ext + 6 * (int64_t)l + d, lo[d]);
+                atomicMax(ext + 6 * (int64_t)l + 3 + d, hi[d]);
+            }
+        }
+    }
+}
+
+// Bounding box of each leaf (or group) from its extents, one thread per box:
+// FP64 reference point near the box centre, FP32 half extents around it
+// rounded up, FP32 reference point relative to the ground cell's lower
+// corner.
 //
 // The reference point is the centre rounded to a multiple of U = 2^(e-24),
 // the FP32 spacing of the box's largest |coordinate| (2^(e-1) <= m < 2^e),
@@ -296,51 +369,18 @@ __device__ __forceinline__ double dkey_inv(long long k)
 // is done as (c + 1.5 2^52 U) - 1.5 2^52 U (round half to even).  Being a
 // multiple of U below 2^e in magnitude, it is itself an FP32 number: r4
 // holds that exact FP32 copy.
-__global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const double *xw, const uint64_t *keys,
+__global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const long long *ext, const uint64_t *keys,
                         const BoxDev *boxes, int T, double *ref, float4 *r4, float4 *c4, float4 *h4,
                         int32_t *cell_of, int32_t *box_of)
 {
     const int count = *scan_total;
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int l0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; l0 < count; l0 += warps * 32) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
         long long lo[3], hi[3];
-        const int nbox = count - l0 < 32 ? count - l0 : 32;
-        for (int j = 0; j < nbox; j++) {
-            const int a = first[l0 + j], e = first[l0 + j + 1];
-            long long jl[3], jh[3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) jl[d] = jh[d] = dkey(xw[3 * (int64_t)a + d]);
-            for (int k = a + 1 + lane; k < e; k += 32) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    const long long v = dkey(xw[3 * (int64_t)k + d]);
-                    jl[d] = v < jl[d] ? v : jl[d];
-                    jh[d] = v > jh[d] ? v : jh[d];
-                }
-            }
-            if (e - a > 1) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        const long long vl = __shfl_xor_sync(0xffffffffu, jl[d], o);
-                        const long long vh = __shfl_xor_sync(0xffffffffu, jh[d], o);
-                        jl[d] = vl < jl[d] ? vl : jl[d];
-                        jh[d] = vh > jh[d] ? vh : jh[d];
-                    }
-                }
-            }
-            if (lane == j) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    lo[d] = jl[d];
-                    hi[d] = jh[d];
-                }
-            }
+        for (int d = 0; d < 3; d++) {
+            lo[d] = ext[6 * (int64_t)l + d];
+            hi[d] = ext[6 * (int64_t)l + 3 + d];
         }
-        if (lane >= nbox) continue;
-        const int l = l0 + lane;
         const uint64_t key = keys[first[l]];
         const int bi = 3 * T < 64 ? (int)(key >> (3 * T)) : 0;
         const BoxDev &bx = boxes[bi];
@@ -460,8 +500,12 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     uint64_t *keys = static_cast<uint64_t *>(h->keys.p);
     int32_t *vals = static_cast<int32_t *>(h->vals.p);
     if (n > 0) {
-        k_keys<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, n, box_first, nb, boxes, T, h->key_kind, keys, vals,
-                                               status);
+        if (pos_type == PH_F64)
+            k_keys<PH_F64><<<grid_for(n), kThreads, 0, s>>>(pos, n, box_first, nb, boxes, T, h->key_kind, keys, vals,
+                                                            status);
+        else
+            k_keys<PH_F32><<<grid_for(n), kThreads, 0, s>>>(pos, n, box_first, nb, boxes, T, h->key_kind, keys, vals,
+                                                            status);
         count_launch();
         bool alt = false;
         int box_bits = 0;
@@ -483,7 +527,10 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     int32_t *lflag = static_cast<int32_t *>(h->leaf_flag.p), *gflag = static_cast<int32_t *>(h->group_flag.p);
     int32_t *lscan = static_cast<int32_t *>(h->leaf_scan.p), *gscan = static_cast<int32_t *>(h->group_scan.p);
     if (n > 0)
-        k_gather<<<grid_for(n), kThreads, 0, s>>>(pos, pos_type, mass, n, sk, perm, boxes, T, xw, ms, status);
+        if (pos_type == PH_F64)
+            k_gather<PH_F64><<<grid_for(n), kThreads, 0, s>>>(pos, mass, n, sk, perm, boxes, T, xw, ms, status);
+        else
+            k_gather<PH_F32><<<grid_for(n), kThreads, 0, s>>>(pos, mass, n, sk, perm, boxes, T, xw, ms, status);
         count_launch();
     k_cell_first<<<grid_for(h->n_cells + 1), kThreads, 0, s>>>(sk, n, boxes, nb, h->n_cells, T, cell_first);
     count_launch();
@@ -496,26 +543,36 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     rc = scan_exclusive_i32(gflag, gscan, n, nullptr, h->temp.p, s);
     if (rc) return rc;
     int32_t *lfirst = static_cast<int32_t *>(h->leaf_first.p), *gfirst = static_cast<int32_t *>(h->group_first.p);
-    if (n > 0) {
-        k_firsts<<<grid_for(n), kThreads, 0, s>>>(lflag, lscan, n, lfirst);
+    long long *ext = static_cast<long long *>(h->box_ext.p);
+    // leaves, then groups: first particles (and extent reset), extents, boxes
+    for (int pass = 0; pass < 2; pass++) {
+        const int32_t *flag = pass ? gflag : lflag;
+        const int32_t *scan = pass ? gscan : lscan;
+        int32_t *first = pass ? gfirst : lfirst;
+        if (n > 0) {
+            k_firsts<<<grid_for(n), kThreads, 0, s>>>(flag, scan, n, first, ext);
+            count_launch();
+            k_extents<<<grid_for(n), kThreads, 0, s>>>(xw, n, scan, ext);
+            count_launch();
+        } else {
+            cudaMemsetAsync(first, 0, sizeof(int32_t), s);
+        }
+        if (pass == 0)
+            k_boxes<<<grid_for(n), kThreads, 0, s>>>(lfirst, lscan + n, ext, sk, boxes, T,
+                                                     static_cast<double *>(h->leaf_ref.p),
+                                                     static_cast<float4 *>(h->leaf_r4.p),
+                                                     static_cast<float4 *>(h->leaf_c4.p),
+                                                     static_cast<float4 *>(h->leaf_h4.p), nullptr, nullptr);
+        else
+            k_boxes<<<grid_for(n), kThreads, 0, s>>>(gfirst, gscan + n, ext, sk, boxes, T,
+                                                     static_cast<double *>(h->group_ref.p),
+                                                     static_cast<float4 *>(h->group_r4.p),
+                                                     static_cast<float4 *>(h->group_c4.p),
+                                                     static_cast<float4 *>(h->group_h4.p),
+                                                     static_cast<int32_t *>(h->group_cell.p),
+                                                     static_cast<int32_t *>(h->group_box.p));
         count_launch();
-        k_firsts<<<grid_for(n), kThreads, 0, s>>>(gflag, gscan, n, gfirst);
-        count_launch();
-    } else {
-        cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
-        cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
     }
-    const int box_grid = sm_count() * 16;   // one warp per box, grid-stride
-    k_boxes<<<box_grid, kThreads, 0, s>>>(lfirst, lscan + n, xw, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
-                                          static_cast<float4 *>(h->leaf_r4.p), static_cast<float4 *>(h->leaf_c4.p),
-                                          static_cast<float4 *>(h->leaf_h4.p), nullptr, nullptr);
-    count_launch();
-    k_boxes<<<box_grid, kThreads, 0, s>>>(gfirst, gscan + n, xw, sk, boxes, T,
-                                          static_cast<double *>(h->group_ref.p), static_cast<float4 *>(h->group_r4.p),
-                                          static_cast<float4 *>(h->group_c4.p), static_cast<float4 *>(h->group_h4.p),
-                                          static_cast<int32_t *>(h->group_cell.p),
-                                          static_cast<int32_t *>(h->group_box.p));
-    count_launch();
     if (n > 0)
         k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
                                                static_cast<const float4 *>(h->leaf_r4.p),

@@ -135,6 +135,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     memset(&bx, 0, sizeof bx);
     const int T = 21;
     bx.L = p.L;
+    bx.L_up = float_at_or_above(p.L);
     bx.g = g;
     bx.b = T - g;
     bx.nside = nside;
@@ -192,6 +193,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     c.take(lv.group_h4, 16 * N);
     c.take(lv.leaf_r4, 16 * N);
     c.take(lv.group_r4, 16 * N);
+    c.take(lv.box_ext, 48 * N);
     c.take(lv.group_cell, 4 * N);
     c.take(lv.group_box, 4 * N);
     c.take(lv.pos_leaf, 16 * N);

@@ -49,7 +49,16 @@ struct BoxDev {
     float s2;
     float eps2s;       // max(eps^2 s2, 1e-12)
     float c_g;
+    float L_up;        // smallest FP32 number >= L: an FP32 x is below L iff x < L_up
 };
+
+// The smallest FP32 number not below L.
+inline float float_at_or_above(double L)
+{
+    float f = (float)L;
+    if ((double)f < L) f = std::nextafter(f, INFINITY);
+    return f;
+}
 
 // Streaming multiprocessors of the current device (persistent grids).
 inline int sm_count()
