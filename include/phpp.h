@@ -209,8 +209,9 @@ int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
 
 /*
  * Autotuner: time the whole step (build, pairs, exact PP) for every
- * combination of leaf_max in {32, 64}, level_bits in {1, 3}, pp_variant in
- * {0, 1} and group_size in {8, 16, 32} on the caller's particles (device buffers; boxes as
+ * combination of leaf_max in {16, 32, 64}, level_bits in {1, 3}, pp_variant
+ * in {0, 1} and group_size in {16, 32} (24 candidates) on the caller's
+ * particles (device buffers; boxes as
  * for ph_build_leaves_batched, n_boxes = 1 for one box) and return the
  * fastest as out->best (params[0] with the winning knobs), with every
  * candidate's median of `reps` timed steps.  The knobs do not change the

@@ -32,10 +32,10 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
     if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
-    const int leaf_sizes[] = {32, 64};
+    const int leaf_sizes[] = {16, 32, 64};
     const int levels[] = {1, 3};
     const int variants[] = {0, 1};
-    const int groups[] = {8, 16, 32};
+    const int groups[] = {16, 32};
     std::vector<ph_params> prm(params, params + n_boxes);
     memset(out, 0, sizeof *out);
     out->best_ms = 3.0e38f;
