@@ -50,9 +50,14 @@ UNIT = "interactions/s"
 #   ->  3 FADD + 7 FMUL + 17 FFMA = 44 flop.
 FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
-# DRAM traffic per PP launch (bytes) from the ncu capture summarised in
-# profiles/pp_exact_zeldovich64.md, or None when the kernel changed since.
-PP_TRAFFIC_BYTES = None
+# DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice
+# with leaf_max 32, binary levels, 32-particle groups, kernel shape 0, from the
+# ncu capture summarised in profiles/pp_exact_zeldovich64.md: that capture is
+# the same configuration on the 64^3 lattice (25.59 MB per launch), scaled by
+# the evaluated pairs of a full launch (3.474e9 / 4.585e8); None for any other
+# configuration, or once the kernel has changed since the capture.
+PP_TRAFFIC_BYTES = 25.589e6 * 3.474e9 / 4.585e8
+PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32)   # workload, scale, leaf_max, level_bits, pp_variant, group
 
 
 def _env_int(k, d):
@@ -400,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
     peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                    # TFLOP/s
     achieved = computed * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": PP_TRAFFIC_BYTES,
+            "traffic": PP_TRAFFIC_BYTES if (args.workload, args.scale, prm.leaf_max, prm.level_bits or 1, prm.pp_variant,
+                                             prm.group_size or 32) == PP_TRAFFIC_CONFIG else None,
             "kernel": "k_pp (exact factor)", "flops_per_interaction": FLOPS_PER_INTERACTION,
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
     if clk and clk.get("sm_mhz"):
@@ -410,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload + (f"@{args.scale}" if args.scale else ""), "n": ps.n, "leaf_max": prm.leaf_max,
-                   "key": "hilbert" if args.key else "morton", "group_size": 32,
+                   "key": "hilbert" if args.key else "morton", "group_size": prm.group_size or 32,
                    "l2": "flushed between steps (256 MB write), per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": t_e2e,
@@ -426,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if tune_info is not None:
         line["config"]["tuned"] = {"leaf_max": prm.leaf_max, "level_bits": prm.level_bits,
-                                   "pp_variant": prm.pp_variant, "cache": tune_info["cache"]}
+                                   "pp_variant": prm.pp_variant, "group_size": prm.group_size or 32,
+                                   "cache": tune_info["cache"]}
     if not args.no_extras:
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
         line["batched"] = _batched_extra(B, args, dev, stream)
