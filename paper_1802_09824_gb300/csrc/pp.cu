@@ -316,8 +316,8 @@ struct Round {
 // Source staging and summation for one target group.  Entries are taken 32
 // at a time, one per lane; the lanes' leaf sizes are prefix-summed and the
 // concatenated source particles are loaded 32 per round, each lane finding
-// the entry of its particle by a binary search over the prefix sums, so that
-// every lane loads a useful particle whatever the leaf sizes.  Kept sources
+// the entry of its particle from the start bits of the round (see Round), so
+// that every lane loads a useful particle whatever the leaf sizes.  Kept sources
 // are written as pairs into the warp's buffer; a full buffer is summed.
 // kMinBlocks: resident 8-warp blocks per SM the register budget must allow
 // (2: up to 128 registers, deeper unrolled pair loop; 3: up to 80).
