@@ -3,7 +3,9 @@
 // Each pass: per-tile digit histograms (digit-major layout), one exclusive
 // scan over all (digit, tile) counts, then a scatter in which every tile
 // ranks its keys stably (warp by warp, 32 keys at a time, with
-// __match_any_sync) and writes them after the keys of earlier tiles.
+// __match_any_sync), reorders them by digit in shared memory and writes each
+// digit's run after the keys of earlier tiles with consecutive threads on
+// consecutive positions.
 #include <utility>
 
 #include "phpp_internal.cuh"
@@ -39,12 +41,17 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *keys, 
 {
     __shared__ int32_t cnt[kSortWarps][kBins];
     __shared__ int32_t s_off[kBins];
+    __shared__ int32_t s_start[kBins];          // first slot of each digit in the tile
+    __shared__ int32_t s_wsum[kSortWarps];
+    __shared__ uint64_t s_key[kSortTile];
+    __shared__ int32_t s_val[kSortTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < kBins; d += 32) cnt[w][d] = 0;
     s_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncwarp();
     // warp w owns keys [base + w*256, base + (w+1)*256), 32 per round, in order
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * 32 * kSortItems;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)w * 32 * kSortItems;
     const unsigned lt = (1u << lane) - 1u;
     uint64_t k_[kSortItems];
     int32_t v_[kSortItems];
@@ -70,24 +77,50 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *keys, 
         r_[r] = old + __popc(peers & lt);
     }
     __syncthreads();
-    {   // exclusive prefix of the per-warp counts over warps, per digit
-        int d = threadIdx.x;
+    {   // per digit: exclusive prefix of the per-warp counts over warps, and
+        // the digit's total in the tile
+        const int d = threadIdx.x;
         int run = 0;
 #pragma unroll
         for (int ww = 0; ww < kSortWarps; ww++) {
-            int c = cnt[ww][d];
+            const int c = cnt[ww][d];
             cnt[ww][d] = run;
             run += c;
         }
+        // exclusive scan of the totals over digits (block-wide)
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_wsum[w] = incl;
+        __syncthreads();
+        int wbase = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ww++) wbase += ww < w ? s_wsum[ww] : 0;
+        s_start[d] = wbase + incl - run;
     }
     __syncthreads();
+    // the tile in digit order in shared memory ...
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
         if (d_[r] < kBins) {
-            int64_t pos = (int64_t)s_off[d_[r]] + cnt[w][d_[r]] + r_[r];
-            keys_out[pos] = k_[r];
-            vals_out[pos] = v_[r];
+            const int slot = s_start[d_[r]] + cnt[w][d_[r]] + r_[r];
+            s_key[slot] = k_[r];
+            s_val[slot] = v_[r];
         }
+    }
+    __syncthreads();
+    // ... then written out slot by slot: consecutive threads write consecutive
+    // positions of a digit's run
+    const int tile_n = n - tile0 < kSortTile ? (int)(n - tile0) : kSortTile;
+    for (int slot = threadIdx.x; slot < tile_n; slot += kSortThreads) {
+        const uint64_t key = s_key[slot];
+        const int d = (int)((key >> shift) & (kBins - 1));
+        const int64_t pos = (int64_t)s_off[d] + (slot - s_start[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = s_val[slot];
     }
 }
 
