@@ -261,6 +261,34 @@ def _batched_extra(B, args, dev, stream):
             "value_graph": n_within / (t_graph * 1e-3), "unit": UNIT}
 
 
+class Ranks:
+    """Barrier and max / sum reductions of one float over the ranks of a
+    torch.distributed job (dist = None: a single process, identity).  The
+    replicas' step times combine by max, their counts by sum."""
+
+    def __init__(self, dist, device):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -301,25 +329,14 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    ranks = Ranks(dist, dev)
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    max_over_ranks = ranks.max
+    sum_over_ranks = ranks.sum
 
     ps = synth.workload(args.workload, scale=args.scale or None)
     bp = ps.boxes[0]
