@@ -255,10 +255,11 @@ typedef struct ph_leaves_view {
     const int32_t *perm;       /* [n] sorted position -> caller row            */
     const int32_t *leaf_first; /* [n_leaves+1]                                 */
     const double  *leaf_ref;   /* [n_leaves*3] leaf reference point (FP64)     */
-    const float   *leaf_half;  /* [n_leaves*4] bounding-box half extents       */
+    const float   *leaf_half;  /* [n_leaves*4] bounding-box half extents x, y,
+                                  z; w holds the particle count (int bits)   */
     const int32_t *group_first;/* [n_groups+1]                                 */
     const double  *group_ref;  /* [n_groups*3]                                 */
-    const float   *group_half; /* [n_groups*4]                                 */
+    const float   *group_half; /* [n_groups*4] as leaf_half                    */
     const float   *pos_leaf;   /* [n*4] x-ref_leaf, y, z, mass (FP32)          */
     const float   *pos_group;  /* [n*4] x-ref_group, y, z, mass (FP32)         */
     const int32_t *cell_leaf_first; /* [n_cells+1] first leaf of each cell     */

@@ -273,7 +273,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     ENS(h->group_h4, 16 * N);
     ENS(h->leaf_r4, 16 * N);
     ENS(h->group_r4, 16 * N);
-    ENS(h->box_ext, 48 * N);
+    ENS(h->box_ext, 96 * N);
     ENS(h->group_cell, 4 * N);
     ENS(h->group_box, 4 * N);
     ENS(h->pos_leaf, 16 * N);

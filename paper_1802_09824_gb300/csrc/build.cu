@@ -285,21 +285,34 @@ __global__ void k_flags(const uint64_t *keys, int64_t n, const BoxDev *boxes, in
     }
 }
 
-// First particle of every leaf (or group); also resets the box's extent
-// accumulators (ordered-integer min and max per axis) for k_extents.
-__global__ void k_firsts(const int32_t *flag, const int32_t *scan, int64_t n, int32_t *first, long long *ext)
+// First particle of every leaf and every group; also resets the boxes'
+// extent accumulators (ordered-integer min and max per axis) for k_extents.
+__global__ void k_firsts(const int32_t *lflag, const int32_t *lscan, const int32_t *gflag, const int32_t *gscan,
+                         int64_t n, int32_t *lfirst, int32_t *gfirst, long long *lext, long long *gext)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        if (flag[k]) {
-            const int64_t l = scan[k];
-            first[l] = (int32_t)k;
+        if (lflag[k]) {
+            const int64_t l = lscan[k];
+            lfirst[l] = (int32_t)k;
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                ext[6 * l + d] = LLONG_MAX;
-                ext[6 * l + 3 + d] = LLONG_MIN;
+                lext[6 * l + d] = LLONG_MAX;
+                lext[6 * l + 3 + d] = LLONG_MIN;
             }
         }
-        if (k == n - 1) first[scan[n]] = (int32_t)n;
+        if (gflag[k]) {
+            const int64_t l = gscan[k];
+            gfirst[l] = (int32_t)k;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                gext[6 * l + d] = LLONG_MAX;
+                gext[6 * l + 3 + d] = LLONG_MIN;
+            }
+        }
+        if (k == n - 1) {
+            lfirst[lscan[n]] = (int32_t)n;
+            gfirst[gscan[n]] = (int32_t)n;
+        }
     }
 }
 
@@ -315,46 +328,53 @@ __device__ __forceinline__ double dkey_inv(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
-// Per-axis extents of every leaf (or group), one thread per particle: the
-// particles of a box are consecutive, so a warp combines each box's part of
-// its 32 particles by a segmented reduction (shuffle down within runs of the
-// same box), and the first lane of each run folds that into the box's
+// Per-axis extents of every leaf and every group, one thread per particle:
+// the particles of a box are consecutive, so a warp combines each box's part
+// of its 32 particles by a segmented reduction (shuffle down within runs of
+// the same box), and the first lane of each run folds that into the box's
 // accumulators with 64-bit atomic min/max (boxes may straddle warps).
 // Coordinates enter as ordered integers (dkey), so the integer order is the
 // FP64 order.
-__global__ void k_extents(const double *xw, int64_t n, const int32_t *scan, long long *ext)
+__device__ __forceinline__ void segment_extent(const long long v[3], int l, int lane, long long *ext)
+{
+    long long lo[3] = {v[0], v[1], v[2]}, hi[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int lo_l = __shfl_down_sync(0xffffffffu, l, o);
+        const bool same = lane + o < 32 && lo_l == l;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const long long vl = __shfl_down_sync(0xffffffffu, lo[d], o);
+            const long long vh = __shfl_down_sync(0xffffffffu, hi[d], o);
+            if (same) {
+                lo[d] = vl < lo[d] ? vl : lo[d];
+                hi[d] = vh > hi[d] ? vh : hi[d];
+            }
+        }
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, l, 1);
+    if (l >= 0 && (lane == 0 || prev != l)) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            atomicMin(ext + 6 * (int64_t)l + d, lo[d]);
+            atomicMax(ext + 6 * (int64_t)l + 3 + d, hi[d]);
+        }
+    }
+}
+
+__global__ void k_extents(const double *xw, int64_t n, const int32_t *lscan, const int32_t *gscan, long long *lext,
+                          long long *gext)
 {
     const int lane = threadIdx.x & 31;
     const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     for (int64_t base = k0; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = base + lane;
         const bool in = k < n;
-        const int l = in ? scan[k + 1] - 1 : -1;
-        long long lo[3], hi[3];
+        long long v[3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) lo[d] = hi[d] = in ? dkey(xw[3 * k + d]) : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int lo_l = __shfl_down_sync(0xffffffffu, l, o);
-            const bool same = lane + o < 32 && lo_l == l;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const long long vl = __shfl_down_sync(0xffffffffu, lo[d], o);
-                const long long vh = __shfl_down_sync(0xffffffffu, hi[d], o);
-                if (same) {
-                    lo[d] = vl < lo[d] ? vl : lo[d];
-                    hi[d] = vh > hi[d] ? vh : hi[d];
-                }
-            }
-        }
-        const int prev = __shfl_up_sync(0xffffffffu, l, 1);
-        if (in && (lane == 0 || prev != l)) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                atomicMin(ext + 6 * (int64_t)l + d, lo[d]);
-                atomicMax(ext + 6 * (int64_t)l + 3 + d, hi[d]);
-            }
-        }
+        for (int d = 0; d < 3; d++) v[d] = in ? dkey(xw[3 * k + d]) : 0;
+        segment_extent(v, in ? lscan[k + 1] - 1 : -1, lane, lext);
+        segment_extent(v, in ? gscan[k + 1] - 1 : -1, lane, gext);
     }
 }
 
@@ -403,8 +423,9 @@ __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const l
             hh[d] = __double2float_ru(half);
         }
         r4[l] = make_float4(rf[0], rf[1], rf[2], 0.f);
-        c4[l] = make_float4(c[0], c[1], c[2], 0.f);
-        h4[l] = make_float4(hh[0], hh[1], hh[2], 0.f);
+        const int f0 = first[l];
+        c4[l] = make_float4(c[0], c[1], c[2], __int_as_float(f0));              // w: first particle
+        h4[l] = make_float4(hh[0], hh[1], hh[2], __int_as_float(first[l + 1] - f0));   // w: particles
         if (cell_of) cell_of[l] = bx.cell_base + (int)ground;
         if (box_of) box_of[l] = bi;
     }
@@ -543,36 +564,29 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     rc = scan_exclusive_i32(gflag, gscan, n, nullptr, h->temp.p, s);
     if (rc) return rc;
     int32_t *lfirst = static_cast<int32_t *>(h->leaf_first.p), *gfirst = static_cast<int32_t *>(h->group_first.p);
-    long long *ext = static_cast<long long *>(h->box_ext.p);
-    // leaves, then groups: first particles (and extent reset), extents, boxes
-    for (int pass = 0; pass < 2; pass++) {
-        const int32_t *flag = pass ? gflag : lflag;
-        const int32_t *scan = pass ? gscan : lscan;
-        int32_t *first = pass ? gfirst : lfirst;
-        if (n > 0) {
-            k_firsts<<<grid_for(n), kThreads, 0, s>>>(flag, scan, n, first, ext);
-            count_launch();
-            k_extents<<<grid_for(n), kThreads, 0, s>>>(xw, n, scan, ext);
-            count_launch();
-        } else {
-            cudaMemsetAsync(first, 0, sizeof(int32_t), s);
-        }
-        if (pass == 0)
-            k_boxes<<<grid_for(n), kThreads, 0, s>>>(lfirst, lscan + n, ext, sk, boxes, T,
-                                                     static_cast<double *>(h->leaf_ref.p),
-                                                     static_cast<float4 *>(h->leaf_r4.p),
-                                                     static_cast<float4 *>(h->leaf_c4.p),
-                                                     static_cast<float4 *>(h->leaf_h4.p), nullptr, nullptr);
-        else
-            k_boxes<<<grid_for(n), kThreads, 0, s>>>(gfirst, gscan + n, ext, sk, boxes, T,
-                                                     static_cast<double *>(h->group_ref.p),
-                                                     static_cast<float4 *>(h->group_r4.p),
-                                                     static_cast<float4 *>(h->group_c4.p),
-                                                     static_cast<float4 *>(h->group_h4.p),
-                                                     static_cast<int32_t *>(h->group_cell.p),
-                                                     static_cast<int32_t *>(h->group_box.p));
+    long long *lext = static_cast<long long *>(h->box_ext.p), *gext = lext + 6 * (size_t)n;
+    // first particles (and extent reset), extents, then the boxes of leaves and groups
+    if (n > 0) {
+        k_firsts<<<grid_for(n), kThreads, 0, s>>>(lflag, lscan, gflag, gscan, n, lfirst, gfirst, lext, gext);
         count_launch();
+        k_extents<<<grid_for(n), kThreads, 0, s>>>(xw, n, lscan, gscan, lext, gext);
+        count_launch();
+    } else {
+        cudaMemsetAsync(lfirst, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(gfirst, 0, sizeof(int32_t), s);
     }
+    k_boxes<<<grid_for(n), kThreads, 0, s>>>(lfirst, lscan + n, lext, sk, boxes, T, static_cast<double *>(h->leaf_ref.p),
+                                             static_cast<float4 *>(h->leaf_r4.p), static_cast<float4 *>(h->leaf_c4.p),
+                                             static_cast<float4 *>(h->leaf_h4.p), nullptr, nullptr);
+    count_launch();
+    k_boxes<<<grid_for(n), kThreads, 0, s>>>(gfirst, gscan + n, gext, sk, boxes, T,
+                                             static_cast<double *>(h->group_ref.p),
+                                             static_cast<float4 *>(h->group_r4.p),
+                                             static_cast<float4 *>(h->group_c4.p),
+                                             static_cast<float4 *>(h->group_h4.p),
+                                             static_cast<int32_t *>(h->group_cell.p),
+                                             static_cast<int32_t *>(h->group_box.p));
+    count_launch();
     if (n > 0)
         k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
                                                static_cast<const float4 *>(h->leaf_r4.p),

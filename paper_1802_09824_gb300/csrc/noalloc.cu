@@ -193,7 +193,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     c.take(lv.group_h4, 16 * N);
     c.take(lv.leaf_r4, 16 * N);
     c.take(lv.group_r4, 16 * N);
-    c.take(lv.box_ext, 48 * N);
+    c.take(lv.box_ext, 96 * N);
     c.take(lv.group_cell, 4 * N);
     c.take(lv.group_box, 4 * N);
     c.take(lv.pos_leaf, 16 * N);

@@ -119,9 +119,11 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             bool acc = false;
             int l = 0;
             const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
+            float4 lc = make_float4(0.f, 0.f, 0.f, 0.f), lh = lc;   // w: first particle, particles (bits)
             if (q < total) {
                 l = lb + q;
-                const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
+                lc = a.leaf_c4[l];
+                lh = a.leaf_h4[l];
                 const float px = fmaxf(fabsf((lc.x + odx * hc) - gc.x) - (gh.x + lh.x), 0.f);
                 const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
                 const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
@@ -152,10 +154,9 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                         e.y = __double2float_rn((lr[1] + sy * L) - gr[1]);
                         e.z = __double2float_rn((lr[2] + sz * L) - gr[2]);
                     }
-                    const int f0 = a.leaf_first[l];
-                    e.w = __int_as_float(f0);
+                    e.w = lc.w;                                            // first particle (bits)
                     a.ent[pos] = e;
-                    a.ecnt[pos] = (uint8_t)(a.leaf_first[l + 1] - f0 - 1);
+                    a.ecnt[pos] = (uint8_t)(__float_as_int(lh.w) - 1);     // particles - 1
                 } else {
                     atomicOr(a.status, ST_CAPACITY);
                 }
