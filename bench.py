@@ -59,7 +59,7 @@ PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # the evaluated pairs of a full launch (3.474e9 / 4.585e8); None for any other
 # configuration, or once the kernel has changed since the capture.
 PP_TRAFFIC_BYTES = 25.589e6 * 3.474e9 / 4.585e8
-PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32)   # workload, scale, leaf_max, level_bits, pp_variant, group
+PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32, 0)   # workload, scale, leaf_max, levels, variant, group, key
 
 
 def _env_int(k, d):
@@ -439,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = computed * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": PP_TRAFFIC_BYTES if (args.workload, args.scale, prm.leaf_max, prm.level_bits or 1, prm.pp_variant,
-                                             prm.group_size or 32) == PP_TRAFFIC_CONFIG else None,
+                                             prm.group_size or 32, prm.key_kind) == PP_TRAFFIC_CONFIG else None,
             "kernel": "k_pp (exact factor)", "flops_per_interaction": FLOPS_PER_INTERACTION,
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
     if clk and clk.get("sm_mhz"):
@@ -449,7 +449,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload + (f"@{args.scale}" if args.scale else ""), "n": ps.n, "leaf_max": prm.leaf_max,
-                   "key": "hilbert" if args.key else "morton", "group_size": prm.group_size or 32,
+                   "key": "hilbert" if prm.key_kind else "morton", "group_size": prm.group_size or 32,
                    "l2": "flushed between steps (256 MB write), per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": t_e2e,
@@ -466,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
     if tune_info is not None:
         line["config"]["tuned"] = {"leaf_max": prm.leaf_max, "level_bits": prm.level_bits,
                                    "pp_variant": prm.pp_variant, "group_size": prm.group_size or 32,
+                                   "key_kind": prm.key_kind,
                                    "cache": tune_info["cache"]}
     if not args.no_extras:
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)

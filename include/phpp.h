@@ -209,13 +209,13 @@ int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
 
 /*
  * Autotuner: time the whole step (build, pairs, exact PP) for every
- * combination of leaf_max in {16, 32, 64}, level_bits in {1, 3}, pp_variant
- * in {0, 1} and group_size in {16, 32} (24 candidates) on the caller's
- * particles (device buffers; boxes as
- * for ph_build_leaves_batched, n_boxes = 1 for one box) and return the
- * fastest as out->best (params[0] with the winning knobs), with every
- * candidate's median of `reps` timed steps.  The knobs do not change the
- * result beyond FP32 summation order.  Synchronises.
+ * combination of leaf_max in {16, 32, 64}, key_kind in {Morton, Hilbert},
+ * pp_variant in {0, 1} and group_size in {16, 32} (24 candidates, binary
+ * levels) on the caller's particles (device buffers; boxes as for
+ * ph_build_leaves_batched, n_boxes = 1 for one box) and return the fastest
+ * as out->best (params[0] with the winning knobs), with every candidate's
+ * median of `reps` timed steps.  The knobs do not change the result beyond
+ * FP32 summation order.  Synchronises.
  */
 #define PH_TUNE_MAX 32
 typedef struct ph_tune_result {
@@ -227,6 +227,7 @@ typedef struct ph_tune_result {
     int32_t   level_bits[PH_TUNE_MAX];
     int32_t   pp_variant[PH_TUNE_MAX];
     int32_t   group_size[PH_TUNE_MAX];
+    int32_t   key_kind[PH_TUNE_MAX];
 } ph_tune_result;
 
 int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int64_t *box_offsets, int32_t n_boxes,

@@ -70,7 +70,7 @@ class ph_tune_result(ctypes.Structure):
     _fields_ = [("best", ph_params), ("best_ms", ctypes.c_float), ("n_tried", ctypes.c_int32),
                 ("ms", ctypes.c_float * PH_TUNE_MAX), ("leaf_max", ctypes.c_int32 * PH_TUNE_MAX),
                 ("level_bits", ctypes.c_int32 * PH_TUNE_MAX), ("pp_variant", ctypes.c_int32 * PH_TUNE_MAX),
-                ("group_size", ctypes.c_int32 * PH_TUNE_MAX)]
+                ("group_size", ctypes.c_int32 * PH_TUNE_MAX), ("key_kind", ctypes.c_int32 * PH_TUNE_MAX)]
 
 
 class ph_pairs_view(ctypes.Structure):

@@ -1,9 +1,8 @@
-// In-project autotuner: leaf size, leaf hierarchy, target group size and PP
-// kernel shape.
+// In-project autotuner: leaf size, local key (Morton or Peano-Hilbert),
+// target group size and PP kernel shape.
 //
-// Every candidate (leaf_max x level_bits x pp_variant x group_size) runs the
-// whole step on
-// the caller's particles -- build, pairs, PP -- once to warm up and then
+// Every candidate (leaf_max x key_kind x pp_variant x group_size) runs the
+// whole step on the caller's particles -- build, pairs, PP -- once to warm up and then
 // `reps` times under CUDA events; the candidate with the smallest median
 // step time wins.  The result does not depend on the knobs (only the FP32
 // summation order does), so the choice is free to follow the hardware.
@@ -33,21 +32,23 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
     if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
     if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
     const int leaf_sizes[] = {16, 32, 64};
-    const int levels[] = {1, 3};
+    const int keys[] = {PH_KEY_MORTON, PH_KEY_HILBERT};
     const int variants[] = {0, 1};
     const int groups[] = {16, 32};
+    const int lb = 1;   // binary levels (octree levels never measured faster)
     std::vector<ph_params> prm(params, params + n_boxes);
     memset(out, 0, sizeof *out);
     out->best_ms = 3.0e38f;
     ph_leaves *lv = nullptr;
     ph_pairs *pr = nullptr;
     for (int lm : leaf_sizes)
-        for (int lb : levels)
+        for (int kk : keys)
             for (int pv : variants)
             for (int gs : groups) {
                 if (rc || out->n_tried >= PH_TUNE_MAX) break;
                 for (auto &p : prm) {
                     p.leaf_max = lm;
+                    p.key_kind = kk;
                     p.level_bits = lb;
                     p.pp_variant = pv;
                     p.group_size = gs;
@@ -73,6 +74,7 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
                 out->level_bits[k] = lb;
                 out->pp_variant[k] = pv;
                 out->group_size[k] = gs;
+                out->key_kind[k] = kk;
                 if (med < out->best_ms) {
                     out->best_ms = med;
                     out->best = prm[0];

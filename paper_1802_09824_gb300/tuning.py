@@ -3,8 +3,8 @@
 The timing itself runs in the library; this module only remembers the
 winning knobs per workload signature so that a workload of the same shape
 is not re-tuned: the number of boxes, the particle count and the mean
-number of particles per ground cell (rounded to a factor of 1.5), R_cut/R_s
-and the key kind.
+number of particles per ground cell (rounded to a factor of 1.5) and
+R_cut/R_s.  The key kind is one of the tuned knobs.
 """
 from __future__ import annotations
 
@@ -12,7 +12,7 @@ import json
 import math
 import os
 
-KNOBS = ("leaf_max", "level_bits", "pp_variant", "group_size")
+KNOBS = ("leaf_max", "level_bits", "pp_variant", "group_size", "key_kind")
 
 
 def default_cache_path() -> str:
@@ -35,7 +35,7 @@ def signature(box_offsets, params_list) -> str:
     dbin = round(math.log(max(dens, 1e-9)) / math.log(1.5))
     nbin = round(math.log(max(n, 1)) / math.log(1.5))
     p0 = params_list[0]
-    return f"b{nb}-n{nbin}-d{dbin}-u{p0.rcut / p0.rs:.4g}-k{p0.key_kind}"
+    return f"b{nb}-n{nbin}-d{dbin}-u{p0.rcut / p0.rs:.4g}"
 
 
 def load(path=None) -> dict:
@@ -77,6 +77,7 @@ def tuned(B, pos, mass, box_offsets, params_list, reps=3, path=None, retune=Fals
     res = B.ph_autotune(pos, mass, box_offsets, params_list, reps)
     knobs = {k: int(getattr(res.best, k)) for k in KNOBS}
     tried = [{"leaf_max": res.leaf_max[i], "level_bits": res.level_bits[i], "pp_variant": res.pp_variant[i],
-              "group_size": res.group_size[i], "ms": float(res.ms[i])} for i in range(res.n_tried)]
+              "group_size": res.group_size[i], "key_kind": res.key_kind[i], "ms": float(res.ms[i])}
+             for i in range(res.n_tried)]
     store(key, knobs, float(res.best_ms), path)
     return apply(params_list, knobs), {"cache": "miss", "key": key, "ms": float(res.best_ms), "tried": tried}

@@ -127,12 +127,12 @@ def test_autotuner_picks_a_tried_candidate(gpu_lib, tmp_path):
     ms = np.array(res.ms[:res.n_tried])
     assert np.all(ms > 0) and abs(res.best_ms - ms.min()) < 1e-6
     k = int(np.argmin(ms))
-    assert (res.best.leaf_max, res.best.level_bits, res.best.pp_variant, res.best.group_size) == (
-        res.leaf_max[k], res.level_bits[k], res.pp_variant[k], res.group_size[k])
+    assert (res.best.leaf_max, res.best.level_bits, res.best.pp_variant, res.best.group_size, res.best.key_kind) == (
+        res.leaf_max[k], res.level_bits[k], res.pp_variant[k], res.group_size[k], res.key_kind[k])
     p2, info = tuning.tuned(B, pos, mass, ps.offsets, _params(B, ps), reps=1, path=str(tmp_path / "t.json"))
     assert info["cache"] == "miss"
     got, lv, pr = gpu_accel(B, ps, leaf_max=p2[0].leaf_max, level_bits=p2[0].level_bits,
-                            group_size=p2[0].group_size)
+                            group_size=p2[0].group_size, key_kind=p2[0].key_kind)
     check_parity(got, oracle_accel(ps))
     B.ph_free(pr)
     B.ph_free(lv)

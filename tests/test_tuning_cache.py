@@ -21,6 +21,8 @@ class FakeLib:
         r.level_bits = [1, 3]
         r.pp_variant = [0, 1]
         r.group_size = [32, 16]
+        r.key_kind = [0, 1]
+        r.best.key_kind = 1
         return r
 
 
@@ -30,11 +32,11 @@ def test_tuned_caches_and_applies(tmp_path):
     offs = np.array([0, 4096])
     p1, info1 = tuning.tuned(FakeLib(), None, None, offs, prm, path=path)
     assert info1["cache"] == "miss" and FakeLib.calls == 1
-    assert (p1[0].leaf_max, p1[0].level_bits, p1[0].pp_variant, p1[0].group_size) == (48, 3, 1, 16)
+    assert (p1[0].leaf_max, p1[0].level_bits, p1[0].pp_variant, p1[0].group_size, p1[0].key_kind) == (48, 3, 1, 16, 1)
     prm2 = [B.make_params(1.0, 1.0, 1e-3, 1.25 / 32, 4.5 * 1.25 / 32, 32)]
     p2, info2 = tuning.tuned(FakeLib(), None, None, offs, prm2, path=path)
     assert info2["cache"] == "hit" and FakeLib.calls == 1
-    assert (p2[0].leaf_max, p2[0].level_bits, p2[0].pp_variant, p2[0].group_size) == (48, 3, 1, 16)
+    assert (p2[0].leaf_max, p2[0].level_bits, p2[0].pp_variant, p2[0].group_size, p2[0].key_kind) == (48, 3, 1, 16, 1)
 
 
 def test_signature_separates_shapes():
