@@ -53,13 +53,14 @@ UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice
-# with leaf_max 32, binary levels, 32-particle groups, kernel shape 0, from the
-# ncu capture summarised in profiles/pp_exact_zeldovich64.md: that capture is
-# the same configuration on the 64^3 lattice (25.59 MB per launch), scaled by
-# the evaluated pairs of a full launch (3.474e9 / 4.585e8); None for any other
-# configuration, or once the kernel has changed since the capture.
-PP_TRAFFIC_BYTES = 25.589e6 * 3.474e9 / 4.585e8
-PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32, 0)   # workload, scale, leaf_max, levels, variant, group, key
+# with leaf_max 32, binary levels, 32-particle groups, kernel shape 0 and
+# Peano-Hilbert keys, from the ncu capture summarised in
+# profiles/pp_exact_zeldovich64.md: that capture is the same configuration on
+# the 64^3 lattice (25.33 MB per launch), scaled by the evaluated pairs of a
+# full launch (3.447e9 / 4.488e8); None for any other configuration, or once
+# the kernel has changed since the capture.
+PP_TRAFFIC_BYTES = 25.331e6 * 3.447e9 / 4.48774e8
+PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32, 1)   # workload, scale, leaf_max, levels, variant, group, key
 
 
 def _env_int(k, d):
