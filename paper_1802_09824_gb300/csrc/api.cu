@@ -186,11 +186,12 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->n = n;
     h->n_boxes = nb;
     {
-        // key bits per axis: enough for cells ~128 times finer than the mean
+        // key bits per axis: enough for cells ~64 times finer than the mean
         // spacing of the most populated box (deeper cells never hold more
         // than leaf_max particles outside strong clustering; cells that do
         // are cut into runs), capped by the 63-bit key and at least 4 bits
-        // below the ground grid
+        // below the ground grid.  The sort takes ceil((3 T + box bits) / 8)
+        // passes: 5 for 2^21 particles in one box.
         int64_t nmax = 1;
         int gmax = 0;
         for (int b = 0; b < nb; b++) {
@@ -200,7 +201,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         int lg = 0;
         while ((int64_t)1 << (3 * lg) < nmax) lg++;     // ceil(log2(cbrt(nmax)))
         const int cap = key_bits_per_axis(nb);
-        h->key_bits = std::min(cap, std::max(lg + 7, gmax + 4));
+        h->key_bits = std::min(cap, std::max(lg + 6, gmax + 4));
     }
     h->max_leaf = params[0].leaf_max;
     h->key_kind = params[0].key_kind;
