@@ -165,7 +165,12 @@ int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity);
  * PP direct summation over the pair list (Eq. (split), Sec. 3.3, Sec. 4.4):
  * writes acc[3*i .. 3*i+2] = a_i for every particle, in the caller's
  * original order (box-concatenated order for batched handles).
- *   g_mode  PH_G_EXACT or PH_G_LEARNED (then mlp must be non-NULL).
+ *   pairs   a list from ph_leaf_pairs on these leaves, or NULL for the direct
+ *           mode (exact factor only): the PP kernel finds each group's leaf
+ *           pairs itself, with the same test and in the same order as
+ *           ph_leaf_pairs, so no list is stored and the result is the same
+ *           bit for bit.
+ *   g_mode  PH_G_EXACT or PH_G_LEARNED (then mlp and pairs must be non-NULL).
  *   acc     [n*3] float32, host or device.
  * Returns PH_WARN_FALLBACK when the learned factor's validated error is above
  * its tolerance: the exact factor is used instead.
@@ -176,6 +181,7 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode,
 /*
  * Whole step in one call: build leaves, pairs, then PP, reusing *leaves and
  * *pairs (created when NULL).  pos/mass/acc host or device as above.
+ * pairs = NULL: build, then the direct-mode PP (no list; exact factor only).
  */
 int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n,
              const ph_params *params, int g_mode, const ph_mlp *mlp, float *acc,
@@ -183,7 +189,8 @@ int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n,
 
 /*
  * Capture the whole step (build, pairs, PP) for these handles as one CUDA
- * graph: one replay launches every kernel of the step -- the PP part one
+ * graph (pairs = NULL: build and the direct-mode PP, exact factor only, no
+ * list and no capacity): one replay launches every kernel of the step -- the PP part one
  * persistent launch over all boxes of a batched handle -- with no host
  * synchronisation and no allocation (the batched, graph-captured execution
  * of the many-box workload; Sec. 4.3's task queue over all boxes' groups).
@@ -283,8 +290,10 @@ int ph_leaves_get_view(const ph_leaves *leaves, ph_leaves_view *out);
 int ph_pairs_get_view(const ph_pairs *pairs, ph_pairs_view *out);
 
 /* Work counted by the last ph_pp_accel on this handle (synchronises):
- * interactions evaluated by the PP kernel, and the j-particles staged. */
-int ph_pp_counters(const ph_pairs *pairs, int64_t *interactions, int64_t *staged);
+ * interactions evaluated by the PP kernel, and the j-particles staged.
+ * `handle` is the pairs handle of that call, or its leaves handle after a
+ * direct-mode call (pairs = NULL). */
+int ph_pp_counters(const void *handle, int64_t *interactions, int64_t *staged);
 
 /* Number of ordered pairs (i, j), j != i, with r_ij < rcut in the lists,
  * decided in FP32 exactly as ph_pp_accel decides its cutoff: the work the

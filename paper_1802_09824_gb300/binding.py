@@ -238,20 +238,22 @@ def ph_pairs_reserve(capacity, pairs=None):
 
 
 def ph_pp_accel(leaves, pairs, g_mode, mlp, acc, stream=None):
-    """Accelerations into ``acc`` [N,3] float32 (host or device), caller order."""
-    return _check(lib().ph_pp_accel(leaves.ptr, pairs.ptr, int(g_mode),
+    """Accelerations into ``acc`` [N,3] float32 (host or device), caller order.
+    pairs = None: the direct mode (leaf pairs found in the kernel)."""
+    return _check(lib().ph_pp_accel(leaves.ptr, pairs.ptr if pairs is not None else None, int(g_mode),
                                     mlp.ptr if mlp is not None else None, _ptr(acc), _stream(stream)))
 
 
-def ph_accel(pos, mass, params, g_mode, mlp, acc, stream=None, leaves=None, pairs=None):
-    """Whole step: build, pairs, PP.  Returns (leaves, pairs) handles for reuse."""
+def ph_accel(pos, mass, params, g_mode, mlp, acc, stream=None, leaves=None, pairs=None, direct=False):
+    """Whole step: build, pairs, PP.  Returns (leaves, pairs) handles for reuse.
+    direct=True: build and the direct-mode PP, no pair list (pairs is None)."""
     lo = _handle_in(leaves)
     po = _handle_in(pairs)
     rc = lib().ph_accel(_ptr(pos), _pos_type(pos), _ptr(mass), int(pos.shape[0]), ctypes.byref(params), int(g_mode),
                         mlp.ptr if mlp is not None else None, _ptr(acc), _stream(stream), ctypes.byref(lo),
-                        ctypes.byref(po))
+                        None if direct else ctypes.byref(po))
     lh = _wrap(lo, leaves, (pos, mass)) if lo.value else None
-    ph = _wrap(po, pairs) if po.value else None
+    ph = _wrap(po, pairs) if (po.value and not direct) else None
     _check(rc)
     return lh, ph
 
@@ -269,10 +271,12 @@ def ph_last_error():
     return lib().ph_last_error().decode()
 
 
-def ph_pp_counters(pairs):
+def ph_pp_counters(handle):
+    """(interactions evaluated, sources staged) of the last PP call: the pairs
+    handle it used, or its leaves handle after a direct-mode call."""
     a = ctypes.c_int64(0)
     b = ctypes.c_int64(0)
-    _check(lib().ph_pp_counters(pairs.ptr, ctypes.byref(a), ctypes.byref(b)))
+    _check(lib().ph_pp_counters(handle.ptr, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
 
 
@@ -335,7 +339,8 @@ def ph_mlp_loss_grad(weights, z0, target, stream=None):
 def ph_graph_create(leaves, pairs, pos, mass, g_mode, mlp, acc, headroom=0.25, stream=None):
     """Capture build + pairs + PP for these handles as one CUDA graph."""
     out = ctypes.c_void_p(None)
-    _check(lib().ph_graph_create(leaves.ptr, pairs.ptr, _ptr(pos), _pos_type(pos), _ptr(mass), int(g_mode),
+    _check(lib().ph_graph_create(leaves.ptr, pairs.ptr if pairs is not None else None, _ptr(pos), _pos_type(pos),
+                                 _ptr(mass), int(g_mode),
                                  mlp.ptr if mlp is not None else None, _ptr(acc), float(headroom), _stream(stream),
                                  ctypes.byref(out)))
     return Handle(out.value, (leaves, pairs, pos, mass, acc, mlp))

@@ -139,7 +139,7 @@ static void free_leaves(ph_leaves *h)
     DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
                       &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
                       &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
-                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->group_cell, &h->group_box,
+                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->work, &h->acc_tmp, &h->group_cell, &h->group_box,
                       &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
     for (DevBuf *b : bufs) release(*b);
 }
@@ -275,6 +275,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     ENS(h->leaf_r4, 16 * N);
     ENS(h->group_r4, 16 * N);
     ENS(h->box_ext, 96 * N);
+    ENS(h->work, 64);
     ENS(h->group_cell, 4 * N);
     ENS(h->group_box, 4 * N);
     ENS(h->pos_leaf, 16 * N);
@@ -435,11 +436,12 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
                 void *stream)
 {
     if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
-    if (!pairs || pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
-    if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    if (pairs && pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
+    if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
     if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP))
         return fail(PH_ERR_ARG, "PH_G_LEARNED needs a ph_mlp handle");
+    if (g_mode == PH_G_LEARNED && !pairs) return fail(PH_ERR_ARG, "PH_G_LEARNED needs a pair list (pairs = NULL)");
     if (leaves->n > 0 && !acc) return fail(PH_ERR_ARG, "acc must not be NULL");
     // the exact path judges the network: its validated error and the
     // rcut / rs it was trained for decide whether it may stand in
@@ -464,20 +466,23 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ph_pairs *pr = const_cast<ph_pairs *>(pairs);
+    ph_leaves *lvm = const_cast<ph_leaves *>(leaves);
     if (leaves->n == 0) return PH_OK;
     const bool dev = is_device_ptr(acc);
     float *dacc = acc;
     int rc = 0;
     if (!dev) {
-        rc = ensure(pr->acc_tmp, (size_t)leaves->n * 12);
+        DevBuf &tmp = pr ? pr->acc_tmp : lvm->acc_tmp;
+        rc = ensure(tmp, (size_t)leaves->n * 12);
         if (rc) return rc;
-        dacc = static_cast<float *>(pr->acc_tmp.p);
+        dacc = static_cast<float *>(tmp.p);
     }
     rc = use_learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), dacc, s)
                      : pp_exact_device(leaves, pairs, dacc, s);
     if (!rc && !dev)
         rc = cuda_check(cudaMemcpyAsync(acc, dacc, (size_t)leaves->n * 12, cudaMemcpyDeviceToHost, s), "copy acc");
-    pr->last_stream = s;
+    if (pr) pr->last_stream = s;
+    else lvm->last_stream = s;
     if (!rc && g_mode == PH_G_LEARNED && !use_learned) return fail(PH_WARN_FALLBACK, "exact factor used: %s", why);
     return rc;
 }
@@ -485,9 +490,10 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
 int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params, int g_mode,
              const ph_mlp *mlp, float *acc, void *stream, ph_leaves **leaves, ph_pairs **pairs)
 {
-    if (!leaves || !pairs) return fail(PH_ERR_ARG, "leaves and pairs must not be NULL");
+    if (!leaves) return fail(PH_ERR_ARG, "leaves must not be NULL");
     int rc = ph_build_leaves(pos, pos_type, mass, n, params, stream, leaves);
     if (rc) return rc;
+    if (!pairs) return ph_pp_accel(*leaves, nullptr, g_mode, mlp, acc, stream);   // direct mode
     rc = ph_leaf_pairs(*leaves, stream, pairs);
     if (rc) return rc;
     return ph_pp_accel(*leaves, *pairs, g_mode, mlp, acc, stream);
@@ -608,12 +614,27 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
 
 int64_t ph_launch_counter(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
-int ph_pp_counters(const ph_pairs *p, int64_t *interactions, int64_t *staged)
+int ph_pp_counters(const void *handle, int64_t *interactions, int64_t *staged)
 {
-    if (!p || p->kind != KIND_PAIRS) return fail(PH_ERR_ARG, "bad arguments");
+    if (!handle) return fail(PH_ERR_ARG, "bad arguments");
+    const uint32_t kind = *static_cast<const uint32_t *>(handle);
+    const void *work = nullptr;
+    cudaStream_t st = nullptr;
+    if (kind == KIND_PAIRS) {
+        const ph_pairs *p = static_cast<const ph_pairs *>(handle);
+        work = p->work.p;
+        st = p->last_stream;
+    } else if (kind == KIND_LEAVES) {
+        const ph_leaves *l = static_cast<const ph_leaves *>(handle);
+        work = l->work.p;
+        st = l->last_stream;
+    } else {
+        return fail(PH_ERR_ARG, "not a pairs or leaves handle");
+    }
     unsigned long long v[3] = {0, 0, 0};
-    int rc = cuda_check(cudaMemcpyAsync(v, p->work.p, 24, cudaMemcpyDeviceToHost, p->last_stream), "read counters");
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(p->last_stream), "counter sync");
+    if (!work) return fail(PH_ERR_STATE, "no PP work recorded on this handle");
+    int rc = cuda_check(cudaMemcpyAsync(v, work, 24, cudaMemcpyDeviceToHost, st), "read counters");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "counter sync");
     if (rc) return rc;
     if (interactions) *interactions = (int64_t)v[1];
     if (staged) *staged = (int64_t)v[2];

@@ -44,9 +44,10 @@ extern "C" {
 int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int pos_type, const float *d_mass,
                     int g_mode, const ph_mlp *mlp, float *d_acc, double headroom, void *stream, ph_graph **out)
 {
-    if (!leaves || leaves->kind != KIND_LEAVES || !pairs || pairs->kind != KIND_PAIRS || !out)
-        return fail(PH_ERR_ARG, "ph_graph_create: leaves, pairs and out must be valid");
-    if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    if (!leaves || leaves->kind != KIND_LEAVES || (pairs && pairs->kind != KIND_PAIRS) || !out)
+        return fail(PH_ERR_ARG, "ph_graph_create: leaves and out must be valid, pairs valid or NULL");
+    if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    if (!pairs && g_mode != PH_G_EXACT) return fail(PH_ERR_ARG, "ph_graph_create: the direct mode is exact only");
     if (leaves->n > 0 && (!d_pos || !d_acc || !is_device_ptr(d_pos) || !is_device_ptr(d_acc) ||
                           (d_mass && !is_device_ptr(d_mass))))
         return fail(PH_ERR_ARG, "ph_graph_create: pos, mass and acc must be device memory");
@@ -55,16 +56,18 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP)) return fail(PH_ERR_ARG, "learned mode needs mlp");
     if (!(headroom >= 0 && headroom < 100)) return fail(PH_ERR_ARG, "headroom must be in [0, 100)");
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
-    // fixed pair capacity with headroom over the current list
-    const int64_t want = (int64_t)((double)pairs->n_pairs * (1.0 + headroom)) + 1024;
-    if (want > pairs->capacity) {
-        int rc = cuda_check(cudaStreamSynchronize(caller), "sync before growing");
-        if (!rc) rc = ensure(pairs->entries, (size_t)want * sizeof(float4));
-        if (!rc) rc = ensure(pairs->ecount, (size_t)want);
-        if (rc) return rc;
-        pairs->capacity = want;
+    if (pairs) {
+        // fixed pair capacity with headroom over the current list
+        const int64_t want = (int64_t)((double)pairs->n_pairs * (1.0 + headroom)) + 1024;
+        if (want > pairs->capacity) {
+            int rc = cuda_check(cudaStreamSynchronize(caller), "sync before growing");
+            if (!rc) rc = ensure(pairs->entries, (size_t)want * sizeof(float4));
+            if (!rc) rc = ensure(pairs->ecount, (size_t)want);
+            if (rc) return rc;
+            pairs->capacity = want;
+        }
+        pairs->fixed_capacity = true;
     }
-    pairs->fixed_capacity = true;
     bool learned = false;
     if (g_mode == PH_G_LEARNED) {
         learned = mlp->max_rel_err <= mlp->tol;
@@ -78,9 +81,9 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     if (!rc) rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (!rc) {
         int rc2 = cuda_check(cudaMemsetAsync(leaves->status.p, 0, 4, s), "clear status");
-        if (!rc2) rc2 = cuda_check(cudaMemsetAsync(pairs->status.p, 0, 4, s), "clear status");
+        if (!rc2 && pairs) rc2 = cuda_check(cudaMemsetAsync(pairs->status.p, 0, 4, s), "clear status");
         if (!rc2) rc2 = build_leaves_device(leaves, d_pos, pos_type, d_mass, s);
-        if (!rc2) rc2 = build_pairs_device(leaves, pairs, s, false);
+        if (!rc2 && pairs) rc2 = build_pairs_device(leaves, pairs, s, false);
         if (!rc2 && leaves->n > 0)
             rc2 = learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), d_acc, s)
                           : pp_exact_device(leaves, pairs, d_acc, s);
@@ -99,7 +102,7 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     // the capture only recorded the launches; do not count them as run
     count_launch((int)-g->kernels);
     leaves->last_stream = caller;
-    pairs->last_stream = caller;
+    if (pairs) pairs->last_stream = caller;
     *out = g;
     if (g_mode == PH_G_LEARNED && !learned)
         return fail(PH_WARN_FALLBACK, "exact factor captured: validated network error %.3e above %.1e",

@@ -39,6 +39,8 @@ struct ph_leaves {
     phpp::DevBuf group_c4, group_h4;      // float4[n]
     phpp::DevBuf leaf_r4, group_r4;       // float4[n]: the reference points in FP32 (exact; see k_boxes)
     phpp::DevBuf box_ext;                 // long long[12 n]: extent accumulators of leaves, then groups (build scratch)
+    phpp::DevBuf work;                    // direct-mode PP: group queue and counters (32 B)
+    phpp::DevBuf acc_tmp;                 // direct-mode PP into a host buffer: device copy of acc
     phpp::DevBuf group_cell;     // int32[n] global ground cell of each group
     phpp::DevBuf group_box;      // int32[n]
     phpp::DevBuf pos_leaf;       // float4[n]

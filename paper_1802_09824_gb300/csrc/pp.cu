@@ -73,6 +73,13 @@ struct PPArgs {
     // constants shared by every box (the uniform kernels read them straight
     // from the parameter bank instead of holding them in registers)
     PairConsts uc;
+    // the leaf-pair walk of the direct mode (no stored list)
+    const int32_t *group_cell;       // global ground cell of each group
+    const float4 *group_c4;          // group box centre in its cell frame
+    const float4 *group_r4, *leaf_r4;   // reference points in FP32 (exact)
+    const double *group_ref, *leaf_ref; // the same in FP64 (periodic images)
+    const float4 *leaf_c4, *leaf_h4; // leaf boxes; w: first particle, particles (int bits)
+    const int32_t *cell_leaf_first;  // first leaf of each ground cell
 };
 
 struct Kahan3 {
@@ -271,6 +278,15 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 struct EntryBatch {
     float4 ent;
     int base, excl, total;
+    // this lane's entry given directly (cnt = 0: no entry)
+    __device__ __forceinline__ void set(float4 e, int cnt, int lane)
+    {
+        ent = e;
+        const int incl = warp_incl_scan_i(cnt, lane);
+        excl = incl - cnt;
+        base = __float_as_int(ent.w) - excl;
+        total = __shfl_sync(0xffffffffu, incl, 31);
+    }
     __device__ __forceinline__ void load(const PPArgs &a, int64_t eb, int64_t e1, int lane)
     {
         const int64_t e = eb + lane;
@@ -442,6 +458,226 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
     }
 }
 
+// Direct mode (exact factor): k_pp without a stored pair list.  Each group's
+// leaf pairs are found here as the pair builder finds them -- lane t < 27
+// takes neighbour cell t, the candidate leaves are box-tested in the same
+// order -- and queued until 32 make a batch, so the batches, the staging and
+// the sums are those of k_pp over the list, bit for bit.
+template <int NPOLY, int kMinBlocks, int kSplit, bool kUniform>
+__global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp_walk(PPArgs a)
+{
+    __shared__ float4 sA[kPPWarps][kJBuf / 2];
+    __shared__ float4 sB[kPPWarps][kJBuf / 2];
+    // direct mode: cell runs and the queue of found entries
+    __shared__ int2 sRun[kPPWarps][32];
+    __shared__ float4 sQEnt[kPPWarps][64];
+    __shared__ int sQCnt[kPPWarps][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    float4 *A = sA[w], *Bq = sB[w];
+    float *Af = reinterpret_cast<float *>(A), *Bf = reinterpret_cast<float *>(Bq);
+    const int ng = *a.n_groups;
+    unsigned long long inter = 0, staged = 0;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(a.queue, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const int i0 = a.group_first[g], ni = a.group_first[g + 1] - i0;
+        const BoxDev &bx = a.boxes[a.group_box[g]];
+        PairConsts cl;
+        if (!kUniform) {
+#pragma unroll
+            for (int q = 0; q <= NPOLY; q++) cl.poly[q] = pk(bx.poly[q], bx.poly[q]);
+            cl.s2 = pk(bx.s2, bx.s2);
+            cl.eps2s = pk(bx.eps2s, bx.eps2s);
+            cl.c_t = pk(bx.c_t, bx.c_t);
+            cl.c_e = pk(bx.c_e, bx.c_e);
+            cl.m1 = pk(-1.f, -1.f);
+            cl.rcut2 = bx.rcut2;
+            cl.rfilt2 = bx.rfilt2;
+        }
+        const PairConsts &c = kUniform ? a.uc : cl;
+        const float rf2 = c.rfilt2;
+        const float4 gh = a.group_h4[g];
+        constexpr int G = 32 / kSplit;
+        const int ti = lane & (G - 1), hs = lane / G;   // target slot, source slot
+        const float4 xi4 = ti < ni ? a.pos_group[i0 + ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const f2_t xi = pk(xi4.x, xi4.x), yi = pk(xi4.y, xi4.y), zi = pk(xi4.z, xi4.z);
+        Kahan3 k;
+        int nbuf = 0;
+        // The source particles of a batch of (up to) 32 entries, one per lane:
+        // each round loads 32 concatenated particles, one per lane.
+        auto stage_batch = [&](const EntryBatch &bt) {
+            int before = 0;
+            for (int q0 = 0; q0 < bt.total; q0 += 32) {
+                Round cur;
+                cur.issue(a, bt, q0, lane, before);
+                float4 p = cur.p;
+                bool keep = false;
+                if (cur.valid) {
+                    p.x = __fadd_rn(p.x, cur.ox);
+                    p.y = __fadd_rn(p.y, cur.oy);
+                    p.z = __fadd_rn(p.z, cur.oz);
+                    const float qx = fmaxf(fabsf(p.x) - gh.x, 0.f);
+                    const float qy = fmaxf(fabsf(p.y) - gh.y, 0.f);
+                    const float qz = fmaxf(fabsf(p.z) - gh.z, 0.f);
+                    keep = qx * qx + qy * qy + qz * qz < rf2;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const int nk = __popc(bal);
+                if (nbuf + nk > kJBuf) {
+                    const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
+                    __syncwarp();
+                    sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
+                    inter += (unsigned long long)nbuf * ni;
+                    staged += nbuf;
+                    nbuf = 0;
+                    __syncwarp();
+                }
+                if (keep) {
+                    const int idx = nbuf + __popc(bal & lt);
+                    const int m = idx >> 1, sl = idx & 1;
+                    Af[m * 4 + sl] = p.x;
+                    Af[m * 4 + 2 + sl] = p.y;
+                    Bf[m * 4 + sl] = p.z;
+                    Bf[m * 4 + 2 + sl] = p.w;
+                }
+                nbuf += nk;
+            }
+        };
+        {
+            // Direct mode: the leaf pairs of the group are found here, as the
+            // pair builder finds them (same test, same order), and queued
+            // until 32 make a batch.  Lane t < 27 takes neighbour cell t.
+            const int ns = bx.nside;
+            const int ground = a.group_cell[g] - bx.cell_base;
+            const int gx = ground / (ns * ns), gy = (ground / ns) % ns, gz = ground % ns;
+            const float4 gc = a.group_c4[g];
+            const float hc = (float)bx.h;
+            int l0 = 0, cnt = 0;
+            if (lane < 27) {
+                const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+                const int ax = gx + dx, ay = gy + dy, az = gz + dz;
+                const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
+                const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
+                const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+                const int nc = bx.cell_base + ((ax - sx * ns) * ns + (ay - sy * ns)) * ns + (az - sz * ns);
+                const float qx = fmaxf(fmaxf(dx * hc - (gc.x + gh.x), (gc.x - gh.x) - (dx + 1) * hc), 0.f);
+                const float qy = fmaxf(fmaxf(dy * hc - (gc.y + gh.y), (gc.y - gh.y) - (dy + 1) * hc), 0.f);
+                const float qz = fmaxf(fmaxf(dz * hc - (gc.z + gh.z), (gc.z - gh.z) - (dz + 1) * hc), 0.f);
+                if (qx * qx + qy * qy + qz * qz < rf2 * 1.0001f) {
+                    l0 = a.cell_leaf_first[nc];
+                    cnt = a.cell_leaf_first[nc + 1] - l0;
+                }
+            }
+            const int cincl = warp_incl_scan_i(cnt, lane);
+            const int cexcl = cincl - cnt;
+            const int ctotal = __shfl_sync(0xffffffffu, cincl, 31);
+            const unsigned nonempty = __ballot_sync(0xffffffffu, cnt > 0);
+            if (cnt > 0) sRun[w][__popc(nonempty & lt)] = make_int2(lane, l0 - cexcl);
+            __syncwarp();
+            const float4 gr4 = a.group_r4[g];
+            int qn = 0;        // queued entries
+            int runs = 0;      // cell runs started before c0
+            for (int c0 = 0; c0 < ctotal; c0 += 32) {
+                const int q = c0 + lane;
+                const unsigned sq = (unsigned)(cexcl - c0);
+                const unsigned starts = __reduce_or_sync(0xffffffffu, (cnt > 0 && sq < 32u) ? 1u << sq : 0u);
+                const int r = runs + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+                runs += __popc(starts);
+                const int2 ru = sRun[w][r];
+                const int o = ru.x;
+                const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
+                bool acc = false;
+                float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+                int ec = 0;
+                if (q < ctotal) {
+                    const int l = ru.y + q;
+                    const float4 lc = a.leaf_c4[l], lh = a.leaf_h4[l];
+                    const float px = fmaxf(fabsf((lc.x + odx * hc) - gc.x) - (gh.x + lh.x), 0.f);
+                    const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
+                    const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
+                    acc = px * px + py * py + pz * pz < rf2;
+                    if (acc) {
+                        const int ax = gx + odx, ay = gy + ody, az = gz + odz;
+                        const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
+                        const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
+                        const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+                        if ((sx | sy | sz) == 0) {
+                            const float4 lr4 = a.leaf_r4[l];
+                            ent.x = __fsub_rn(lr4.x, gr4.x);
+                            ent.y = __fsub_rn(lr4.y, gr4.y);
+                            ent.z = __fsub_rn(lr4.z, gr4.z);
+                        } else {
+                            const double *lr = a.leaf_ref + 3 * (int64_t)l;
+                            const double *gr = a.group_ref + 3 * (int64_t)g;
+                            const double L = bx.L;
+                            ent.x = __double2float_rn((lr[0] + sx * L) - gr[0]);
+                            ent.y = __double2float_rn((lr[1] + sy * L) - gr[1]);
+                            ent.z = __double2float_rn((lr[2] + sz * L) - gr[2]);
+                        }
+                        ent.w = lc.w;
+                        ec = __float_as_int(lh.w);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                if (acc) {
+                    const int slot = qn + __popc(bal & lt);
+                    sQEnt[w][slot] = ent;
+                    sQCnt[w][slot] = ec;
+                }
+                qn += __popc(bal);
+                __syncwarp();
+                if (qn >= 32) {
+                    EntryBatch bt;
+                    bt.set(sQEnt[w][lane], sQCnt[w][lane], lane);
+                    __syncwarp();
+                    if (lane < qn - 32) {
+                        sQEnt[w][lane] = sQEnt[w][32 + lane];
+                        sQCnt[w][lane] = sQCnt[w][32 + lane];
+                    }
+                    __syncwarp();
+                    qn -= 32;
+                    stage_batch(bt);
+                }
+            }
+            if (qn > 0) {
+                EntryBatch bt;
+                bt.set(lane < qn ? sQEnt[w][lane] : make_float4(0.f, 0.f, 0.f, 0.f), lane < qn ? sQCnt[w][lane] : 0,
+                       lane);
+                stage_batch(bt);
+            }
+            __syncwarp();   // sRun and the queue are rewritten for the next group
+        }
+        const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
+        __syncwarp();
+        sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
+        inter += (unsigned long long)nbuf * ni;
+        staged += nbuf;
+        __syncwarp();
+        // the kSplit source slots of a target add up their compensated totals
+        float tx = k.sx - k.cx, ty = k.sy - k.cy, tz = k.sz - k.cz;
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            tx += __shfl_xor_sync(0xffffffffu, tx, o);
+            ty += __shfl_xor_sync(0xffffffffu, ty, o);
+            tz += __shfl_xor_sync(0xffffffffu, tz, o);
+        }
+        if (hs == 0 && ti < ni) {
+            const int64_t o = a.perm[i0 + ti];
+            const float Gc = bx.c_g;
+            a.acc[3 * o + 0] = Gc * tx;
+            a.acc[3 * o + 1] = Gc * ty;
+            a.acc[3 * o + 2] = Gc * tz;
+        }
+    }
+    if (lane == 0 && inter) {
+        atomicAdd(a.n_inter, inter);
+        atomicAdd(a.n_staged, staged);
+    }
+}
+
 // Number of (i, j) pairs with r^2 < rcut^2 in the lists, self pairs
 // included (each target meets itself once, at d = 0): the work the cutoff
 // keeps, counted with the PP kernel's own FP32 decision.
@@ -520,11 +756,20 @@ static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArg
     a.pos_leaf = static_cast<const float4 *>(lv->pos_leaf.p);
     a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
     a.perm = static_cast<const int32_t *>(lv->keys_in_alt ? lv->vals_alt.p : lv->vals.p);
-    a.group_off = static_cast<const int64_t *>(pr->group_off.p);
-    a.entries = static_cast<const float4 *>(pr->entries.p);
-    a.ecount = static_cast<const uint8_t *>(pr->ecount.p);
-    a.cap = pr->capacity;
-    char *work = static_cast<char *>(pr->work.p);
+    a.group_off = pr ? static_cast<const int64_t *>(pr->group_off.p) : nullptr;
+    a.entries = pr ? static_cast<const float4 *>(pr->entries.p) : nullptr;
+    a.ecount = pr ? static_cast<const uint8_t *>(pr->ecount.p) : nullptr;
+    a.cap = pr ? pr->capacity : 0;
+    a.group_cell = static_cast<const int32_t *>(lv->group_cell.p);
+    a.group_c4 = static_cast<const float4 *>(lv->group_c4.p);
+    a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);
+    a.leaf_r4 = static_cast<const float4 *>(lv->leaf_r4.p);
+    a.group_ref = static_cast<const double *>(lv->group_ref.p);
+    a.leaf_ref = static_cast<const double *>(lv->leaf_ref.p);
+    a.leaf_c4 = static_cast<const float4 *>(lv->leaf_c4.p);
+    a.leaf_h4 = static_cast<const float4 *>(lv->leaf_h4.p);
+    a.cell_leaf_first = static_cast<const int32_t *>(lv->cell_leaf_first.p);
+    char *work = static_cast<char *>(pr ? pr->work.p : lv->work.p);
     a.queue = reinterpret_cast<int32_t *>(work);
     a.n_inter = reinterpret_cast<unsigned long long *>(work + 8);
     a.n_staged = reinterpret_cast<unsigned long long *>(work + 16);
@@ -539,6 +784,38 @@ static void launch_pp(int npoly, int grid, cudaStream_t s, const PPArgs &a)
     case 12: k_pp<12, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
     case 14: k_pp<14, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
     default: k_pp<16, kLearned, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    }
+}
+
+template <int kMinBlocks, int kSplit, bool kUniform>
+static void launch_walk_one(int npoly, int grid, cudaStream_t s, const PPArgs &a)
+{
+    switch (npoly) {
+    case 10: k_pp_walk<10, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    case 12: k_pp_walk<12, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    case 14: k_pp_walk<14, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    default: k_pp_walk<16, kMinBlocks, kSplit, kUniform><<<grid, kPPThreads, 0, s>>>(a); break;
+    }
+}
+
+// The direct-mode kernel for every group size and kernel shape.
+static void launch_walk(const ph_leaves *lv, int npoly, bool uni, cudaStream_t s, const PPArgs &a)
+{
+    const bool three = lv->pp_variant == 1 && uni;
+    const int grid = sm_count() * (three ? kBlocks1 : kBlocks0);
+    const int gs = lv->group_size;
+    if (three) {
+        if (gs == 8) launch_walk_one<kBlocks1, 4, true>(npoly, grid, s, a);
+        else if (gs == 16) launch_walk_one<kBlocks1, 2, true>(npoly, grid, s, a);
+        else launch_walk_one<kBlocks1, 1, true>(npoly, grid, s, a);
+    } else if (uni) {
+        if (gs == 8) launch_walk_one<kBlocks0, 4, true>(npoly, grid, s, a);
+        else if (gs == 16) launch_walk_one<kBlocks0, 2, true>(npoly, grid, s, a);
+        else launch_walk_one<kBlocks0, 1, true>(npoly, grid, s, a);
+    } else {
+        if (gs == 8) launch_walk_one<kBlocks0, 4, false>(npoly, grid, s, a);
+        else if (gs == 16) launch_walk_one<kBlocks0, 2, false>(npoly, grid, s, a);
+        else launch_walk_one<kBlocks0, 1, false>(npoly, grid, s, a);
     }
 }
 
@@ -592,12 +869,17 @@ int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaS
     PPArgs a;
     pp_args(lv, pr, d_acc, a);
     a.mlp_w = nullptr;
-    int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
+    int rc = cuda_check(cudaMemsetAsync(pr ? pr->work.p : lv->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
     const int npoly = lv->poly_degree;
     if (npoly != 10 && npoly != 12 && npoly != 14 && npoly != 16)
         return fail(PH_ERR_STATE, "unsupported polynomial degree %d", npoly);
     const bool uni = uniform_consts(lv, a.uc);
+    if (!pr) {
+        launch_walk(lv, npoly, uni, s, a);
+        count_launch();
+        return cuda_check(cudaGetLastError(), "pp kernel");
+    }
     const bool three = lv->pp_variant == 1;
     const int grid = sm_count() * (three ? kBlocks1 : kBlocks0);
     const int gs = lv->group_size;
