@@ -462,7 +462,11 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 // leaf pairs are found here as the pair builder finds them -- lane t < 27
 // takes neighbour cell t, the candidate leaves are box-tested in the same
 // order -- and queued until 32 make a batch, so the batches, the staging and
-// the sums are those of k_pp over the list, bit for bit.
+// the sums are those of k_pp over the list, bit for bit.  The staging loop
+// is repeated here rather than shared with k_pp: sharing it (a template
+// switch around a common loop) changed the list kernel's register allocation
+// and cost it 2.5 %.  For the same reason the walk's arguments sit at the end
+// of PPArgs.
 template <int NPOLY, int kMinBlocks, int kSplit, bool kUniform>
 __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp_walk(PPArgs a)
 {
