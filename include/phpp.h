@@ -69,6 +69,9 @@ extern "C" {
 /* how the short-range factor f is evaluated in the PP kernel */
 #define PH_G_EXACT    0     /* Eq. (split), FP32 with SFU exp/rsqrt             */
 #define PH_G_LEARNED  1     /* the 1-16-16-1 SiLU network of a ph_mlp           */
+#define PH_G_TABLE    2     /* Eq. (split) tabulated at 4097 nodes in r (the
+                               pre-computed table of Sec. 3.1): nearest node
+                               plus its slope; one rcut and rs for all boxes */
 
 /*
  * Parameters of one periodic box.
@@ -170,7 +173,9 @@ int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity);
  *           pairs itself, with the same test and in the same order as
  *           ph_leaf_pairs, so no list is stored and the result is the same
  *           bit for bit.
- *   g_mode  PH_G_EXACT or PH_G_LEARNED (then mlp and pairs must be non-NULL).
+ *   g_mode  PH_G_EXACT, PH_G_LEARNED (then mlp and pairs must be non-NULL)
+ *           or PH_G_TABLE (pairs must be non-NULL; the table is made on the
+ *           host and uploaded at the first call for an rcut / rs).
  *   acc     [n*3] float32, host or device.
  * Returns PH_WARN_FALLBACK when the learned factor's validated error is above
  * its tolerance: the exact factor is used instead.

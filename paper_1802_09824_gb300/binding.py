@@ -29,7 +29,7 @@ PH_ERR_TIMEOUT = -7
 PH_ERR_STATE = -8
 PH_F32, PH_F64 = 0, 1
 PH_KEY_MORTON, PH_KEY_HILBERT = 0, 1
-PH_G_EXACT, PH_G_LEARNED = 0, 1
+PH_G_EXACT, PH_G_LEARNED, PH_G_TABLE = 0, 1, 2
 
 
 class PhError(RuntimeError):

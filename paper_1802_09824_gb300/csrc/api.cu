@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,40 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
 int count_within_device(const ph_leaves *lv, const ph_pairs *pr, cudaStream_t s);
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s);
+int pp_table_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
+
+// The tabulated factor of PH_G_TABLE for the handle's (single) rs and rcut:
+// f(r_i) = erfc(u) + (2u / sqrt(pi)) exp(-u^2), u = r_i / (2 rs), at
+// r_i = i rcut / 4096, i = 0..4096, with f'(r_i) dr = -(4 u^2 / sqrt(pi))
+// exp(-u^2) / (2 rs) dr, in FP64 then rounded to FP32; uploaded once per
+// (rs, rcut) before any launch that reads it.
+int ensure_table(ph_leaves *lv, cudaStream_t s)
+{
+    if (lv->n_boxes < 1 || (int)lv->boxes_host.size() < lv->n_boxes) return fail(PH_ERR_STATE, "no boxes");
+    const double rcut = std::sqrt((double)lv->boxes_host[0].rcut2);
+    const double rs = std::sqrt(-1.4426950408889634 / (4.0 * (double)lv->boxes_host[0].c_e));
+    for (int b = 1; b < lv->n_boxes; b++)
+        if (lv->boxes_host[b].rcut2 != lv->boxes_host[0].rcut2 || lv->boxes_host[b].c_e != lv->boxes_host[0].c_e)
+            return fail(PH_ERR_ARG, "the tabulated factor needs one rcut and rs for all boxes");
+    if (lv->table.p && lv->table_rs == rs && lv->table_rcut == rcut) return PH_OK;
+    constexpr int N = 4096;
+    std::vector<float> host(2 * (N + 1));
+    const double dr = rcut / N, sqpi = std::sqrt(M_PI);
+    for (int i = 0; i <= N; i++) {
+        const double u = i * dr / (2.0 * rs);
+        const double e = std::exp(-u * u);
+        host[2 * i] = (float)(std::erfc(u) + 2.0 * u / sqpi * e);
+        host[2 * i + 1] = (float)(-4.0 * u * u / sqpi * e / (2.0 * rs) * dr);
+    }
+    int rc = ensure(lv->table, host.size() * sizeof(float));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "sync before table upload");
+    if (!rc) rc = cuda_check(cudaMemcpy(lv->table.p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice),
+                             "upload factor table");
+    if (rc) return rc;
+    lv->table_rs = rs;
+    lv->table_rcut = rcut;
+    return PH_OK;
+}
 void graph_free(ph_graph *g);
 void fit_factor_poly(double U, int deg, float *coef);
 
@@ -139,7 +174,7 @@ static void free_leaves(ph_leaves *h)
     DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
                       &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
                       &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
-                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->work, &h->acc_tmp, &h->group_cell, &h->group_box,
+                      &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->work, &h->acc_tmp, &h->table, &h->group_cell, &h->group_box,
                       &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
     for (DevBuf *b : bufs) release(*b);
 }
@@ -438,10 +473,11 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
     if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
     if (pairs && pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
-    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
+    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED && g_mode != PH_G_TABLE)
+        return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP))
         return fail(PH_ERR_ARG, "PH_G_LEARNED needs a ph_mlp handle");
-    if (g_mode == PH_G_LEARNED && !pairs) return fail(PH_ERR_ARG, "PH_G_LEARNED needs a pair list (pairs = NULL)");
+    if (g_mode != PH_G_EXACT && !pairs) return fail(PH_ERR_ARG, "the learned and tabulated factors need a pair list");
     if (leaves->n > 0 && !acc) return fail(PH_ERR_ARG, "acc must not be NULL");
     // the exact path judges the network: its validated error and the
     // rcut / rs it was trained for decide whether it may stand in
@@ -477,8 +513,13 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
         if (rc) return rc;
         dacc = static_cast<float *>(tmp.p);
     }
-    rc = use_learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), dacc, s)
-                     : pp_exact_device(leaves, pairs, dacc, s);
+    if (g_mode == PH_G_TABLE) {
+        rc = ensure_table(lvm, s);
+        if (!rc) rc = pp_table_device(leaves, pairs, dacc, s);
+    } else {
+        rc = use_learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), dacc, s)
+                         : pp_exact_device(leaves, pairs, dacc, s);
+    }
     if (!rc && !dev)
         rc = cuda_check(cudaMemcpyAsync(acc, dacc, (size_t)leaves->n * 12, cudaMemcpyDeviceToHost, s), "copy acc");
     if (pr) pr->last_stream = s;

@@ -19,6 +19,8 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
 int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s);
+int pp_table_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
+int ensure_table(ph_leaves *lv, cudaStream_t s);
 }  // namespace phpp
 
 struct ph_graph {
@@ -48,11 +50,15 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
         return fail(PH_ERR_ARG, "ph_graph_create: leaves and out must be valid, pairs valid or NULL");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
     if (!pairs && g_mode != PH_G_EXACT) return fail(PH_ERR_ARG, "ph_graph_create: the direct mode is exact only");
+    if (g_mode == PH_G_TABLE) {
+        const int rt = ensure_table(leaves, static_cast<cudaStream_t>(stream));   // before the capture
+        if (rt) return rt;
+    }
     if (leaves->n > 0 && (!d_pos || !d_acc || !is_device_ptr(d_pos) || !is_device_ptr(d_acc) ||
                           (d_mass && !is_device_ptr(d_mass))))
         return fail(PH_ERR_ARG, "ph_graph_create: pos, mass and acc must be device memory");
     if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "bad pos_type");
-    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED) return fail(PH_ERR_ARG, "bad g_mode");
+    if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED && g_mode != PH_G_TABLE) return fail(PH_ERR_ARG, "bad g_mode");
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP)) return fail(PH_ERR_ARG, "learned mode needs mlp");
     if (!(headroom >= 0 && headroom < 100)) return fail(PH_ERR_ARG, "headroom must be in [0, 100)");
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
@@ -85,8 +91,9 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
         if (!rc2) rc2 = build_leaves_device(leaves, d_pos, pos_type, d_mass, s);
         if (!rc2 && pairs) rc2 = build_pairs_device(leaves, pairs, s, false);
         if (!rc2 && leaves->n > 0)
-            rc2 = learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), d_acc, s)
-                          : pp_exact_device(leaves, pairs, d_acc, s);
+            rc2 = g_mode == PH_G_TABLE ? pp_table_device(leaves, pairs, d_acc, s)
+                  : learned ? pp_learned_device(leaves, pairs, static_cast<const float *>(mlp->theta.p), d_acc, s)
+                            : pp_exact_device(leaves, pairs, d_acc, s);
         cudaGraph_t gr = nullptr;
         rc = cuda_check(cudaStreamEndCapture(s, &gr), "end capture");
         g->graph = gr;

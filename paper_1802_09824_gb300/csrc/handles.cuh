@@ -41,6 +41,8 @@ struct ph_leaves {
     phpp::DevBuf box_ext;                 // long long[12 n]: extent accumulators of leaves, then groups (build scratch)
     phpp::DevBuf work;                    // direct-mode PP: group queue and counters (32 B)
     phpp::DevBuf acc_tmp;                 // direct-mode PP into a host buffer: device copy of acc
+    phpp::DevBuf table;                   // PH_G_TABLE: float2[4097] factor nodes (value, slope x spacing)
+    double table_rs = 0.0, table_rcut = 0.0;   // the rs, rcut the table was made for
     phpp::DevBuf group_cell;     // int32[n] global ground cell of each group
     phpp::DevBuf group_box;      // int32[n]
     phpp::DevBuf pos_leaf;       // float4[n]

@@ -80,6 +80,9 @@ struct PPArgs {
     const double *group_ref, *leaf_ref; // the same in FP64 (periodic images)
     const float4 *leaf_c4, *leaf_h4; // leaf boxes; w: first particle, particles (int bits)
     const int32_t *cell_leaf_first;  // first leaf of each ground cell
+    // tabulated factor (PH_G_TABLE): kTabN + 1 nodes (f(r_i), f'(r_i) dr)
+    const float2 *table;
+    float tab_scale2;                // (kTabN / rcut)^2
 };
 
 struct Kahan3 {
@@ -205,6 +208,69 @@ __device__ __forceinline__ void sum_buffer(const float4 *A, const float4 *B, int
         for (; s < nstep; s++) {
             const int m = s * kSplit + h;
             interact2<NPOLY>(A[m], B[m], xi, yi, zi, c, px, py, pz);
+        }
+        k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
+    }
+}
+
+// Tabulated factor (PH_G_TABLE, the pre-computed table of Sec. 3.1): f at
+// kTabN + 1 nodes r_i = i rcut / kTabN with its derivative times the node
+// spacing; a pair takes the node nearest to r and its slope,
+// f = f_i + (r / dr - i) f'_i dr.  The node index comes from the FP32
+// round-to-nearest of r / dr + 1.5 2^23 (exact for r / dr < 2^22), clamped
+// to the last node (pairs beyond rcut are removed by the cutoff select).
+constexpr int kTabN = 4096;
+constexpr float kMagic = 12582912.f;   // 1.5 2^23
+__device__ __forceinline__ void interact2_table(const float4 a, const float4 b, const f2_t xi, const f2_t yi,
+                                                const f2_t zi, const PairConsts &c, const float2 *tab,
+                                                const f2_t scale2, f2_t &px, f2_t &py, f2_t &pz)
+{
+    const f2_t dx = sub2(pk(a.x, a.y), xi), dy = sub2(pk(a.z, a.w), yi), dz = sub2(pk(b.x, b.y), zi);
+    f2_t r2 = mul2(dx, dx);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    const f2_t x = fma2(r2, c.s2, c.eps2s);
+    const f2_t x3 = mul2(mul2(x, x), x);
+    const f2_t inv3 = pk(rsqrt_sfu(lo_of(x3)), rsqrt_sfu(hi_of(x3)));
+    const f2_t q = mul2(r2, scale2);
+    const f2_t u = pk(sqrt_sfu(lo_of(q)), sqrt_sfu(hi_of(q)));   // r / dr
+    const f2_t mg = pk(kMagic, kMagic);
+    const f2_t y = add2(u, mg);
+    const f2_t fr = sub2(u, sub2(y, mg));                            // r / dr - nearest node
+    const int i0 = min(__float_as_int(lo_of(y)) - 0x4B400000, kTabN);
+    const int i1 = min(__float_as_int(hi_of(y)) - 0x4B400000, kTabN);
+    const float2 t0 = tab[i0], t1 = tab[i1];
+    const f2_t f = pk(fmaf(t0.y, lo_of(fr), t0.x), fmaf(t1.y, hi_of(fr), t1.x));
+    const f2_t w = mul2(mul2(pk(b.z, b.w), f), inv3);
+    const float w0 = lo_of(r2) < c.rcut2 ? lo_of(w) : 0.f;
+    const float w1 = hi_of(r2) < c.rcut2 ? hi_of(w) : 0.f;
+    const f2_t wm = pk(w0, w1);
+    px = fma2(wm, dx, px);
+    py = fma2(wm, dy, py);
+    pz = fma2(wm, dz, pz);
+}
+
+template <int kSplit>
+__device__ __forceinline__ void sum_buffer_table(const float4 *A, const float4 *B, int npair, int h, const f2_t xi,
+                                                 const f2_t yi, const f2_t zi, const PairConsts &c,
+                                                 const float2 *tab, const f2_t scale2, Kahan3 &k)
+{
+    const int nstep = npair / kSplit;
+    int s = 0;
+    for (; s + kRun <= nstep; s += kRun) {
+        f2_t px = 0ull, py = 0ull, pz = 0ull;
+#pragma unroll
+        for (int u = 0; u < kRun; u++) {
+            const int m = (s + u) * kSplit + h;
+            interact2_table(A[m], B[m], xi, yi, zi, c, tab, scale2, px, py, pz);
+        }
+        k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
+    }
+    if (s < nstep) {
+        f2_t px = 0ull, py = 0ull, pz = 0ull;
+        for (; s < nstep; s++) {
+            const int m = s * kSplit + h;
+            interact2_table(A[m], B[m], xi, yi, zi, c, tab, scale2, px, py, pz);
         }
         k.add(lo_of(px) + hi_of(px), lo_of(py) + hi_of(py), lo_of(pz) + hi_of(pz));
     }
@@ -340,11 +406,12 @@ struct Round {
 // kSplit: lanes per target (target groups of 32 / kSplit particles).
 // kUniform: every box has the same factor constants, read from the kernel's
 // parameter bank (no registers); else they are loaded per group.
-template <int NPOLY, bool kLearned, int kMinBlocks, int kSplit, bool kUniform>
+template <int NPOLY, bool kLearned, int kMinBlocks, int kSplit, bool kUniform, bool kTable = false>
 __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
     __shared__ float4 sB[kPPWarps][kJBuf / 2];
+    extern __shared__ float2 sTab[];   // kTable: the factor table (dynamic shared memory)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     float4 *A = sA[w], *Bq = sB[w];
@@ -353,6 +420,10 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
     unsigned long long inter = 0, staged = 0;
     MlpLane L;
     if (kLearned) mlp_lane_load(a.mlp_w, L);
+    if (kTable) {
+        for (int i = threadIdx.x; i <= kTabN; i += blockDim.x) sTab[i] = a.table[i];
+        __syncthreads();
+    }
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(a.queue, 1);
@@ -409,6 +480,9 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                     __syncwarp();
                     if (kLearned)
                         sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+                    else if (kTable)
+                        sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab,
+                                                 pk(a.tab_scale2, a.tab_scale2), k);
                     else
                         sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
                     inter += (unsigned long long)nbuf * ni;
@@ -431,6 +505,8 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         __syncwarp();
         if (kLearned)
             sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+        else if (kTable)
+            sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab, pk(a.tab_scale2, a.tab_scale2), k);
         else
             sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
         inter += (unsigned long long)nbuf * ni;
@@ -823,6 +899,20 @@ static void launch_walk(const ph_leaves *lv, int npoly, bool uni, cudaStream_t s
     }
 }
 
+constexpr int kTabBytes = (kTabN + 1) * (int)sizeof(float2);
+
+template <int kSplit>
+static void launch_table_one(int grid, cudaStream_t s, const PPArgs &a)
+{
+    static bool ready = false;
+    if (!ready) {
+        cudaFuncSetAttribute(k_pp<10, false, kBlocks0, kSplit, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes);
+        ready = true;
+    }
+    k_pp<10, false, kBlocks0, kSplit, true, true><<<grid, kPPThreads, kTabBytes, s>>>(a);
+}
+
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s)
 {
     PPArgs a;
@@ -866,6 +956,26 @@ static bool uniform_consts(const ph_leaves *lv, PairConsts &uc)
     uc.rcut2 = b0.rcut2;
     uc.rfilt2 = b0.rfilt2;
     return true;
+}
+
+// PP with the tabulated factor (every box shares one rcut and rs; the table
+// is lv->table, filled by the caller for them).
+int pp_table_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)
+{
+    PPArgs a;
+    pp_args(lv, pr, d_acc, a);
+    a.mlp_w = nullptr;
+    if (!uniform_consts(lv, a.uc)) return fail(PH_ERR_ARG, "the tabulated factor needs one rcut and rs for all boxes");
+    a.table = static_cast<const float2 *>(lv->table.p);
+    a.tab_scale2 = (float)((kTabN / lv->table_rcut) * (kTabN / lv->table_rcut));
+    int rc2 = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
+    if (rc2) return rc2;
+    const int grid = sm_count() * kBlocks0;
+    if (lv->group_size == 8) launch_table_one<4>(grid, s, a);
+    else if (lv->group_size == 16) launch_table_one<2>(grid, s, a);
+    else launch_table_one<1>(grid, s, a);
+    count_launch();
+    return cuda_check(cudaGetLastError(), "table pp kernel");
 }
 
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s)

@@ -99,3 +99,48 @@ def test_direct_mode_refuses_the_learned_factor(gpu_lib):
     assert ei.value.code == B.PH_ERR_ARG
     B.ph_free(lv)
     B.ph_free(m)
+
+
+@pytest.mark.parametrize("name,scale,gs", [("zeldovich_128", 32, 0), ("nfw_mix_256", 20, 16),
+                                            ("uniform_small", 3000, 8)])
+def test_tabulated_factor_matches_the_oracle(gpu_lib, name, scale, gs):
+    """PH_G_TABLE (the factor at 4097 nodes, nearest node plus slope): parity
+    with the FP64 oracle and closeness to the exact factor on the same lists."""
+    import torch
+    B = gpu_lib
+    ps = synth.workload(name, scale=scale)
+    bp = ps.boxes[0]
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, 0, gs)
+    lv = B.ph_build_leaves(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm)
+    pr = B.ph_leaf_pairs(lv)
+    a_ex = torch.zeros((ps.n, 3), dtype=torch.float32, device="cuda")
+    a_tb = torch.zeros((ps.n, 3), dtype=torch.float32, device="cuda")
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, a_ex)
+    c_ex = B.ph_pp_counters(pr)
+    B.ph_pp_accel(lv, pr, B.PH_G_TABLE, None, a_tb)
+    c_tb = B.ph_pp_counters(pr)
+    torch.cuda.synchronize()
+    assert c_tb == c_ex
+    got, ex = a_tb.cpu().numpy(), a_ex.cpu().numpy()
+    check_parity(got, oracle_accel(ps))
+    mag = np.maximum(np.linalg.norm(ex, axis=1, keepdims=True), 1e-30)
+    assert np.max(np.abs(got - ex) / mag) < 1e-3
+    B.ph_free(pr)
+    B.ph_free(lv)
+
+
+def test_tabulated_factor_needs_one_rcut(gpu_lib):
+    import torch
+    B = gpu_lib
+    ps = synth.batch_boxes(3, seed=4, n_min=300, n_max=800)
+    prms = [B.make_params(bp.L, bp.G, bp.eps, bp.rs * (1 + 0.1 * k), bp.rcut * (1 + 0.1 * k), 32)
+            for k, bp in enumerate(ps.boxes)]
+    lv = B.ph_build_leaves_batched(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), ps.offsets,
+                                   prms)
+    pr = B.ph_leaf_pairs(lv)
+    acc = torch.zeros((ps.n, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PhError) as ei:
+        B.ph_pp_accel(lv, pr, B.PH_G_TABLE, None, acc)
+    assert ei.value.code == B.PH_ERR_ARG
+    B.ph_free(pr)
+    B.ph_free(lv)
