@@ -245,6 +245,54 @@ def _table_extra(B, ps, lv, pr, stream, t_exact_pp, flush):
             "force_p99_rel_err_exact": p99(acc_e.cpu().numpy()), "oracle_targets": int(tg.size)}
 
 
+def _tree_extra(B, stream, flush, theta=0.3):
+    """The tree part (leaf monopoles at opening angle theta) on the clustered
+    256^3 NFW mixture: whole-step time against theta = 0 and the force error
+    of both against the plain FP64 oracle on sampled targets."""
+    import torch
+    from oracle import force
+    from paper_1802_09824_gb300 import synth
+    ps = synth.workload("nfw_mix_256")
+    bp = ps.boxes[0]
+    pos = torch.from_numpy(ps.pos).cuda()
+    mass = torch.from_numpy(ps.mass).cuda()
+    rng = np.random.default_rng(13)
+    tg = rng.choice(ps.n, 256, replace=False)
+    ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=tg)
+    am = np.linalg.norm(ref.acc, axis=1)
+    tau = 1e-3 * np.median(am)
+    out = {"workload": "nfw_mix_256", "n": ps.n, "theta": theta, "leaf_max": 32, "key": "hilbert"}
+    for th in (0.0, theta):
+        prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, 1, 32, 1, 0, th)
+        acc = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
+        lv = B.ph_build_leaves(pos, mass, prm, stream)
+        pr = B.ph_leaf_pairs(lv, stream)
+        g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.25, stream=stream)
+        B.ph_graph_launch(g, stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.ph_graph_launch(g, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        B.ph_status(pr)
+        inter, staged = B.ph_pp_counters(pr)
+        a = acc.cpu().numpy()[tg].astype(np.float64)
+        e = np.linalg.norm(a - ref.acc, axis=1) / np.maximum(am, tau)
+        key = "theta0" if th == 0 else "theta"
+        out[key] = {"step_ms": float(np.median(ts)), "pairs_evaluated": inter,
+                    "force_p99_rel_err": float(np.percentile(e, 99)), "force_max_rel_err": float(e.max())}
+        for h in (g, pr, lv):
+            B.ph_free(h)
+    out["speedup_vs_theta0"] = out["theta0"]["step_ms"] / out["theta"]["step_ms"]
+    out["oracle_targets"] = int(tg.size)
+    return out
+
+
 def _batched_extra(B, args, dev, stream):
     """512 boxes: one graph-captured step vs one ph_accel call per box."""
     import torch
@@ -509,6 +557,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
         line["table"] = _table_extra(B, ps, lv, pr, stream, t_pp, flush)
+        line["tree"] = _tree_extra(B, stream, flush)
         line["batched"] = _batched_extra(B, args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, nt, dt, cores = _oracle_rate(ps, args.cpu_seconds)

@@ -95,6 +95,14 @@ extern "C" {
  *   pp_variant PP kernel shape: 0 = two 8-warp blocks per SM (deeper
  *             unrolled source loop), 1 = three blocks per SM (fewer
  *             registers, more warps).  Same results.
+ *   theta     opening criterion of the tree part (Sec. 3.3), in [0, 1):
+ *             0 (default) = every leaf pair by PP (the exact short-range
+ *             sum); theta > 0 = a leaf whose box centre is at distance R >
+ *             (A + B) / theta from the target group's box centre (A, B the
+ *             largest box widths; this implies the second criterion
+ *             B / (R - A) < theta) acts on the group as one particle of the
+ *             leaf's mass at its mass centre, still with the split factor
+ *             and the cutoff.  Tree leaves only (no interior nodes).
  */
 typedef struct ph_params {
     double  L;
@@ -108,6 +116,7 @@ typedef struct ph_params {
     int32_t level_bits;
     int32_t pp_variant;
     int32_t reserved;
+    double  theta;
 } ph_params;
 
 typedef struct ph_leaves ph_leaves;   /* sorted particles + leaf / group tables */

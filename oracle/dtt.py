@@ -99,10 +99,13 @@ def accept(lc, lh, gc, gh, odx, hc, c_acc):
     return bool(R2 > f32(D * D))
 
 
-def accel(pos, mass, L, G, eps, rs, rcut, theta, leaf_max=32, group_size=32, key_kind=0, T=21, level_bits=1):
+def accel(pos, mass, L, G, eps, rs, rcut, theta, leaf_max=32, group_size=32, key_kind=0, T=21, level_bits=1,
+          with_near=False, near_tol=1e-5):
     """Accelerations with leaf monopoles accepted at opening angle theta.
 
-    Returns (acc [n,3] in the caller's order, number of accepted pairs)."""
+    Returns (acc [n,3] in the caller's order, number of accepted pairs), and
+    with ``with_near`` also the summed magnitude of each target's terms within
+    near_tol rcut of the cutoff (which FP32 may keep or drop)."""
     pos = np.asarray(pos, np.float64)
     mass = np.asarray(mass, np.float32)
     n = pos.shape[0]
@@ -121,6 +124,7 @@ def accel(pos, mass, L, G, eps, rs, rcut, theta, leaf_max=32, group_size=32, key
     ltrue_c, ltrue_h = t.leaf_boxes()
     gtrue_c, gtrue_h = t.group_boxes()
     acc_sorted = np.zeros((n, 3))
+    near_sorted = np.zeros(n)
     rcut2, eps2 = rcut * rcut, eps * eps
     n_acc = 0
     for g in range(len(t.group_first) - 1):
@@ -160,8 +164,15 @@ def accel(pos, mass, L, G, eps, rs, rcut, theta, leaf_max=32, group_size=32, key
         self_pair = ids[None, :] == np.arange(i0, i1)[:, None]
         keep = (r2 < rcut2) & ~self_pair
         r = np.sqrt(r2)
-        w = np.where(keep, G * Mw[None, :] * force.split_factor_np(r, rs) / (r2 + eps2) ** 1.5, 0.0)
+        w_all = G * Mw[None, :] * force.split_factor_np(r, rs) / (r2 + eps2) ** 1.5
+        w = np.where(keep, w_all, 0.0)
         acc_sorted[i0:i1] = np.sum(w[:, :, None] * d, axis=1)
+        near = (np.abs(r - rcut) < near_tol * rcut) & ~self_pair
+        near_sorted[i0:i1] = np.sum(np.where(near, np.abs(w_all) * r, 0.0), axis=1)
     acc = np.empty_like(acc_sorted)
     acc[t.order] = acc_sorted
+    if with_near:
+        near_abs = np.empty_like(near_sorted)
+        near_abs[t.order] = near_sorted
+        return acc, n_acc, near_abs
     return acc, n_acc

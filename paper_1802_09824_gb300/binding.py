@@ -42,7 +42,7 @@ class ph_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("G", ctypes.c_double), ("eps", ctypes.c_double),
                 ("rs", ctypes.c_double), ("rcut", ctypes.c_double), ("leaf_max", ctypes.c_int32),
                 ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("level_bits", ctypes.c_int32),
-                ("pp_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("pp_variant", ctypes.c_int32), ("reserved", ctypes.c_int32), ("theta", ctypes.c_double)]
 
 
 class ph_leaves_view(ctypes.Structure):
@@ -168,9 +168,9 @@ def _pos_type(t):
 
 
 def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0, level_bits=0,
-                pp_variant=0):
+                pp_variant=0, theta=0.0):
     return ph_params(float(L), float(G), float(eps), float(rs), float(rcut), int(leaf_max), int(key_kind),
-                     int(group_size), int(level_bits), int(pp_variant), 0)
+                     int(group_size), int(level_bits), int(pp_variant), 0, float(theta))
 
 
 class Handle:

@@ -164,6 +164,8 @@ static int check_params(const ph_params &p, int b)
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3)
         return fail(PH_ERR_ARG, "box %d: level_bits must be 0, 1 or 3", b);
     if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "box %d: pp_variant must be 0 or 1", b);
+    if (!(std::isfinite(p.theta) && p.theta >= 0 && p.theta < 1))
+        return fail(PH_ERR_ARG, "box %d: theta must be in [0, 1)", b);
     if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
         return fail(PH_ERR_ARG, "box %d: rcut/rs = %g above the supported 9.2", b, p.rcut / p.rs);
     return PH_OK;
@@ -252,12 +254,15 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->poly_degree = deg;
     int cells = 0;
     std::vector<int32_t> bf(nb + 1);
+    h->tree_leaves = false;
     for (int b = 0; b < nb; b++) {
         const ph_params &p = params[b];
         BoxDev &bx = h->boxes_host[b];
         memset(&bx, 0, sizeof bx);
         bx.L = p.L;
         bx.L_up = float_at_or_above(p.L);
+        bx.c_acc = p.theta > 0 ? (float)(1.0 / p.theta) : INFINITY;
+        if (p.theta > 0) h->tree_leaves = true;
         bx.g = ground_level(p.L, p.rcut);
         bx.b = h->key_bits - bx.g;
         bx.nside = 1 << bx.g;
@@ -313,7 +318,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     ENS(h->work, 64);
     ENS(h->group_cell, 4 * N);
     ENS(h->group_box, 4 * N);
-    ENS(h->pos_leaf, 16 * N);
+    ENS(h->pos_leaf, 32 * N);
     ENS(h->pos_group, 16 * N);
     ENS(h->cell_leaf_first, 4 * (size_t)(cells + 1));
     ENS(h->counts, 16);
@@ -478,6 +483,7 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP))
         return fail(PH_ERR_ARG, "PH_G_LEARNED needs a ph_mlp handle");
     if (g_mode != PH_G_EXACT && !pairs) return fail(PH_ERR_ARG, "the learned and tabulated factors need a pair list");
+    if (!pairs && leaves->tree_leaves) return fail(PH_ERR_ARG, "the tree part (theta > 0) needs a pair list");
     if (leaves->n > 0 && !acc) return fail(PH_ERR_ARG, "acc must not be NULL");
     // the exact path judges the network: its validated error and the
     // rcut / rs it was trained for decide whether it may stand in

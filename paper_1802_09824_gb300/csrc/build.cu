@@ -431,6 +431,37 @@ __global__ void k_boxes(const int32_t *first, const int32_t *scan_total, const l
     }
 }
 
+// Tree part (theta > 0): one particle per leaf carrying the leaf's mass at
+// its mass centre, sum(m x) / sum(m) over the leaf's wrapped positions in
+// FP64 (summed in particle order), stored after the N particles of pos_leaf
+// relative to the leaf's reference point like the leaf's own particles.  A
+// massless leaf keeps its reference point.
+__global__ void k_leaf_mass(const int32_t *first, const int32_t *scan_total, const double *xw, const float *mass,
+                            const double *ref, int64_t n, float4 *pos_leaf)
+{
+    const int count = *scan_total;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
+        const int a = first[l], e = first[l + 1];
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int k = a; k < e; k++) {
+            const double m = mass[k];
+            M = __dadd_rn(M, m);
+            sx = __dadd_rn(sx, __dmul_rn(m, xw[3 * (int64_t)k]));
+            sy = __dadd_rn(sy, __dmul_rn(m, xw[3 * (int64_t)k + 1]));
+            sz = __dadd_rn(sz, __dmul_rn(m, xw[3 * (int64_t)k + 2]));
+        }
+        const double *r = ref + 3 * (int64_t)l;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (M > 0.0) {
+            q.x = __double2float_rn(__dsub_rn(__ddiv_rn(sx, M), r[0]));
+            q.y = __double2float_rn(__dsub_rn(__ddiv_rn(sy, M), r[1]));
+            q.z = __double2float_rn(__dsub_rn(__ddiv_rn(sz, M), r[2]));
+            q.w = __double2float_rn(M);
+        }
+        pos_leaf[n + l] = q;
+    }
+}
+
 __global__ void k_pos(int64_t n, const double *xw, const float *mass_sorted, const int32_t *leaf_scan,
                       const int32_t *group_scan, const double *leaf_ref, const float4 *leaf_r4, const float4 *group_r4,
                       float4 *pos_leaf, float4 *pos_group)
@@ -587,6 +618,11 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
                                              static_cast<int32_t *>(h->group_cell.p),
                                              static_cast<int32_t *>(h->group_box.p));
     count_launch();
+    if (n > 0 && h->tree_leaves) {
+        k_leaf_mass<<<grid_for(n), kThreads, 0, s>>>(lfirst, lscan + n, xw, ms, static_cast<const double *>(h->leaf_ref.p),
+                                                     n, static_cast<float4 *>(h->pos_leaf.p));
+        count_launch();
+    }
     if (n > 0)
         k_pos<<<grid_for(n), kThreads, 0, s>>>(n, xw, ms, lscan, gscan, static_cast<const double *>(h->leaf_ref.p),
                                                static_cast<const float4 *>(h->leaf_r4.p),

@@ -50,6 +50,7 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
         return fail(PH_ERR_ARG, "ph_graph_create: leaves and out must be valid, pairs valid or NULL");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
     if (!pairs && g_mode != PH_G_EXACT) return fail(PH_ERR_ARG, "ph_graph_create: the direct mode is exact only");
+    if (!pairs && leaves->tree_leaves) return fail(PH_ERR_ARG, "ph_graph_create: the tree part needs a pair list");
     if (g_mode == PH_G_TABLE) {
         const int rt = ensure_table(leaves, static_cast<cudaStream_t>(stream));   // before the capture
         if (rt) return rt;

@@ -18,6 +18,7 @@ struct ph_leaves {
     int32_t key_kind = PH_KEY_MORTON;
     int32_t level_bits = 1;      // key bits per level of the leaf hierarchy (1 or 3)
     int32_t pp_variant = 0;      // PP kernel register/occupancy variant (0: 2 blocks/SM, 1: 3)
+    bool tree_leaves = false;    // some box has theta > 0: leaf mass-centre particles are made
     std::vector<phpp::BoxDev> boxes_host;
     // device buffers
     phpp::DevBuf boxes;          // BoxDev[n_boxes]
@@ -45,7 +46,7 @@ struct ph_leaves {
     double table_rs = 0.0, table_rcut = 0.0;   // the rs, rcut the table was made for
     phpp::DevBuf group_cell;     // int32[n] global ground cell of each group
     phpp::DevBuf group_box;      // int32[n]
-    phpp::DevBuf pos_leaf;       // float4[n]
+    phpp::DevBuf pos_leaf;       // float4[2n]: particles, then one mass-centre particle per leaf (theta > 0)
     phpp::DevBuf pos_group;      // float4[n]
     phpp::DevBuf cell_leaf_first;// int32[n_cells + 1]
     phpp::DevBuf counts;         // int32[4]: n_leaves, n_groups (device copies)

@@ -109,6 +109,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
         return fail(PH_ERR_ARG, "ph_accel_noalloc: L, rs, rcut must be finite and > 0, eps >= 0, G finite");
     if (!(p.rcut < 0.5 * p.L)) return fail(PH_ERR_RCUT_GE_HALF_L, "rcut %g >= L/2 %g", p.rcut, 0.5 * p.L);
     if (p.leaf_max < 1 || p.leaf_max > kMaxLeaf) return fail(PH_ERR_ARG, "leaf_max must be 1..%d", kMaxLeaf);
+    if (p.theta != 0) return fail(PH_ERR_ARG, "ph_accel_noalloc: theta must be 0 (every leaf pair by PP)");
     if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT) return fail(PH_ERR_ARG, "unknown key_kind");
     if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "group_size must be 0 or 32");
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3) return fail(PH_ERR_ARG, "level_bits must be 0, 1 or 3");
@@ -136,6 +137,7 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     const int T = 21;
     bx.L = p.L;
     bx.L_up = float_at_or_above(p.L);
+    bx.c_acc = INFINITY;   // every leaf pair by PP (theta must be 0 here)
     bx.g = g;
     bx.b = T - g;
     bx.nside = nside;

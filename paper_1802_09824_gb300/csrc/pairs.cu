@@ -35,6 +35,7 @@ struct PairArgs {
     float4 *ent;             // fill pass output: offset x, y, z, first source particle (bits)
     uint8_t *ecnt;           // fill pass output: particles in the leaf - 1
     const int32_t *leaf_first;
+    int64_t n_particles;     // mass-centre particle of leaf l: pos_leaf[n_particles + l]
     int64_t cap;
     uint32_t *status;
 };
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             before += __popc(starts);
             const int2 ru = s_run[w][r];
             const int o = ru.x, lb = ru.y;
-            bool acc = false;
+            bool acc = false, mono = false;
             int l = 0;
             const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
             float4 lc = make_float4(0.f, 0.f, 0.f, 0.f), lh = lc;   // w: first particle, particles (bits)
@@ -128,6 +129,19 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                 const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
                 const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
                 acc = px * px + py * py + pz * pz < rf2;
+                // tree part: accepted as one mass-centre particle when the box
+                // centres are further apart than (A + B) / theta (A, B the
+                // largest box widths), decided in FP32 with every rounding fixed
+                if (acc && bx.c_acc < INFINITY) {
+                    const float ex = __fsub_rn(__fadd_rn(lc.x, __fmul_rn((float)odx, hc)), gc.x);
+                    const float ey = __fsub_rn(__fadd_rn(lc.y, __fmul_rn((float)ody, hc)), gc.y);
+                    const float ez = __fsub_rn(__fadd_rn(lc.z, __fmul_rn((float)odz, hc)), gc.z);
+                    const float R2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                    const float A = __fmul_rn(2.f, fmaxf(fmaxf(gh.x, gh.y), gh.z));
+                    const float Bw = __fmul_rn(2.f, fmaxf(fmaxf(lh.x, lh.y), lh.z));
+                    const float D = __fmul_rn(__fadd_rn(A, Bw), bx.c_acc);
+                    mono = R2 > __fmul_rn(D, D);
+                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc);
             if (kFill && acc) {
@@ -154,9 +168,15 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                         e.y = __double2float_rn((lr[1] + sy * L) - gr[1]);
                         e.z = __double2float_rn((lr[2] + sz * L) - gr[2]);
                     }
-                    e.w = lc.w;                                            // first particle (bits)
-                    a.ent[pos] = e;
-                    a.ecnt[pos] = (uint8_t)(__float_as_int(lh.w) - 1);     // particles - 1
+                    if (mono) {
+                        e.w = __int_as_float((int)(a.n_particles + l));  // the leaf's mass-centre particle
+                        a.ent[pos] = e;
+                        a.ecnt[pos] = 0;
+                    } else {
+                        e.w = lc.w;                                        // first particle (bits)
+                        a.ent[pos] = e;
+                        a.ecnt[pos] = (uint8_t)(__float_as_int(lh.w) - 1); // particles - 1
+                    }
                 } else {
                     atomicOr(a.status, ST_CAPACITY);
                 }
@@ -187,6 +207,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.leaf_r4 = static_cast<const float4 *>(lv->leaf_r4.p);
     a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);
     a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
+    a.n_particles = lv->n;
     a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
     a.off = static_cast<const int64_t *>(pr->group_off.p);
     a.status = static_cast<uint32_t *>(pr->status.p);

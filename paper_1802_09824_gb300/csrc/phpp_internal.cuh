@@ -50,6 +50,7 @@ struct BoxDev {
     float eps2s;       // max(eps^2 s2, 1e-12)
     float c_g;
     float L_up;        // smallest FP32 number >= L: an FP32 x is below L iff x < L_up
+    float c_acc;       // 1 / theta of the tree part (infinite: every leaf pair by PP)
 };
 
 // The smallest FP32 number not below L.
