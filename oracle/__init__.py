@@ -13,4 +13,9 @@ Modules:
   tree    -- octree leaves, i-groups and the cutoff leaf-pair relation
   mlp     -- the 1-16-16-1 SiLU network that stands in for the factor:
              forward, backward and Adam in float64
+  dtt     -- the tree part at the leaf level (opening criterion, leaf
+             mass-centre bodies)
+  pm      -- the long-range particle-mesh side (CIC, Green's function of
+             the 3-point difference Laplacian with the split filter, central
+             difference, CIC interpolation), numpy float64
 """
