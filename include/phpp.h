@@ -123,6 +123,7 @@ typedef struct ph_leaves ph_leaves;   /* sorted particles + leaf / group tables 
 typedef struct ph_pairs  ph_pairs;    /* cutoff leaf-pair list (CSR by group)    */
 typedef struct ph_mlp    ph_mlp;      /* learned short-range factor             */
 typedef struct ph_graph  ph_graph;    /* a whole step captured as a CUDA graph  */
+typedef struct ph_pm     ph_pm;       /* long-range particle-mesh solver         */
 
 /*
  * Sort the particles of one box along the space-filling curve and cut them
@@ -254,7 +255,64 @@ typedef struct ph_tune_result {
 int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int64_t *box_offsets, int32_t n_boxes,
                 const ph_params *params, int32_t reps, void *stream, ph_tune_result *out);
 
-/* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph).  NULL is a no-op. */
+/* ------------------------------------------------------------ long-range PM
+ * The particle-mesh side of the force split (Sec. 3.1), which supplies what
+ * the short-range sum leaves out: the total force is ph_pp_accel's short-range
+ * acceleration plus this one.  Steps, in the paper's order:
+ *   1. Cloud-in-Cell assignment of the masses to a periodic N^3 mesh with
+ *      nodes at x = i L/N (64-bit fixed-point sums: the node masses do not
+ *      depend on the order of the additions);
+ *   2. FFT (cuFFT, FP32);
+ *   3. the Green's function of the 3-point difference Laplacian of Sec. 3.1,
+ *      phi_k = -pi G Delta_g^2 rho_k / (sin^2(pi l/N) + sin^2(pi m/N) +
+ *      sin^2(pi n/N)), Delta_g = L/N, rho = node mass / Delta_g^3, times the
+ *      long-range filter exp(-k^2 R_s^2) (k the continuum wavenumber
+ *      2 pi l'/L of the mode, l' in (-N/2, N/2]); the k = 0 mode is dropped
+ *      (neutralising background);
+ *   4. inverse FFT: the potential on the mesh;
+ *   5. a = -grad phi on the mesh by the 2-point central difference, then
+ *      Cloud-in-Cell interpolation to each particle with the assignment
+ *      weights.  No window deconvolution.
+ * The cell of a particle is decided in FP64: x_w = x - L floor(x/L),
+ * u = x_w (N/L), node floor(u) mod N, fraction u - floor(u).
+ *
+ *   pos, pos_type, mass, n   as for ph_build_leaves (host or device; mass
+ *                NULL = 1/n each); one box, caller order.
+ *   params       L, G and rs are used (rs = 0: no filter, the whole
+ *                periodic PM force); the other fields are ignored.
+ *   n_mesh       N, even, 4..PH_PM_MAX_MESH.
+ *   acc          [n*3] float32 host or device: written, or added to when
+ *                accumulate != 0 (e.g. onto ph_pp_accel's result).
+ *   pot          [n] float32 host or device, nullable: the long-range
+ *                potential interpolated to each particle.
+ *   pm           in/out handle (mesh buffers, FFT plans); created when
+ *                *pm == NULL; kept while N is unchanged.
+ * Memory: 44 N^3 bytes + the FFT work area (about 95 MB at N = 128).
+ * Errors: PH_ERR_ARG, PH_ERR_OOM, PH_ERR_CUDA; a non-finite coordinate or
+ * mass is latched (ph_status(pm) reports PH_ERR_NONFINITE) and that
+ * particle is left out.  Synchronises only when acc or pot are host memory
+ * or when the Green's function tables are (re)made for a new N, L or rs.
+ */
+#define PH_PM_MAX_MESH 1024
+
+int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params,
+                int32_t n_mesh, float *acc, float *pot, int32_t accumulate, void *stream, ph_pm **pm);
+
+typedef struct ph_pm_view {
+    int32_t n_mesh;
+    int32_t reserved;
+    double  mass_unit;          /* node mass = mass_fixed[i] * mass_unit        */
+    const int64_t *mass_fixed;  /* [N^3] node masses of step 1, fixed point,
+                                   index (i N + j) N + k for node (i, j, k)     */
+    const float   *mesh;        /* [N^3 * 4] per node: -dphi/dx, -dphi/dy,
+                                   -dphi/dz, phi (steps 4-5, before the
+                                   interpolation)                              */
+} ph_pm_view;
+
+/* Device views of the last ph_pm_accel's meshes (synchronises). */
+int ph_pm_get_view(const ph_pm *pm, ph_pm_view *out);
+
+/* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph, ph_pm).  NULL is a no-op. */
 void ph_free(void *handle);
 
 /* Message of the last failing call on this thread ("" if none). */

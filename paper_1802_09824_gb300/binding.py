@@ -78,6 +78,13 @@ class ph_pairs_view(ctypes.Structure):
                 ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
 
 
+class ph_pm_view(ctypes.Structure):
+    _fields_ = [("n_mesh", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mass_unit", ctypes.c_double),
+                ("mass_fixed", ctypes.c_void_p), ("mesh", ctypes.c_void_p)]
+
+
+PH_PM_MAX_MESH = 1024
+
 _lib = None
 
 _VP = ctypes.c_void_p
@@ -110,6 +117,9 @@ _SIGS = {
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
     "ph_graph_kernels": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ph_pm_accel": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.c_int32, _VP, _VP,
+                     ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_pm_get_view": ([_VP, ctypes.POINTER(ph_pm_view)], ctypes.c_int),
     "ph_autotune": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(ph_params),
                      ctypes.c_int32, _VP, ctypes.POINTER(ph_tune_result)], ctypes.c_int),
 }
@@ -365,6 +375,30 @@ def ph_autotune(pos, mass, box_offsets, params_list, reps=3, stream=None):
     _check(lib().ph_autotune(_ptr(pos), _pos_type(pos), _ptr(mass), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                              nb, arr, int(reps), _stream(stream), ctypes.byref(res)))
     return res
+
+
+def ph_pm_accel(pos, mass, params, n_mesh, acc, pot=None, accumulate=False, stream=None, pm=None):
+    """Long-range PM acceleration into ``acc`` [N,3] (added to it when
+    ``accumulate``), optional potential into ``pot`` [N]; host or device
+    tensors.  Returns the ph_pm handle for reuse."""
+    out = _handle_in(pm)
+    rc = lib().ph_pm_accel(_ptr(pos), _pos_type(pos), _ptr(mass), int(pos.shape[0]), ctypes.byref(params),
+                           int(n_mesh), _ptr(acc), _ptr(pot), int(bool(accumulate)), _stream(stream),
+                           ctypes.byref(out))
+    h = _wrap(out, pm) if out.value else None
+    _check(rc)
+    return h
+
+
+def ph_pm_get_view(pm):
+    """Device views: fixed-point node masses (int64 [N,N,N]) with their unit,
+    and the per-node (-grad phi, phi) mesh (float32 [N,N,N,4])."""
+    v = ph_pm_view()
+    _check(lib().ph_pm_get_view(pm.ptr, ctypes.byref(v)))
+    n = v.n_mesh
+    return {"n_mesh": n, "mass_unit": v.mass_unit,
+            "mass_fixed": _dev(v.mass_fixed, (n, n, n), "<i8"),
+            "mesh": _dev(v.mesh, (n, n, n, 4), "<f4")}
 
 
 def ph_launch_counter():

@@ -54,7 +54,9 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if (not os.path.exists(OUT)) or os.path.getmtime(OUT) < max(os.path.getmtime(o) for o in objs):
-        cmd = [_nvcc(), *ARCH, "-shared", *objs, "-o", OUT + ".tmp", "-lcudart"]
+        libdir = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "lib64")
+        cmd = [_nvcc(), *ARCH, "-shared", *objs, "-o", OUT + ".tmp", "-lcudart", "-lcufft",
+               "-Xlinker", "-rpath", "-Xlinker", libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

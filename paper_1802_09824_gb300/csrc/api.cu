@@ -55,6 +55,8 @@ int ensure_table(ph_leaves *lv, cudaStream_t s)
     return PH_OK;
 }
 void graph_free(ph_graph *g);
+void pm_free(ph_pm *h);
+int pm_status(const ph_pm *h);
 void fit_factor_poly(double U, int deg, float *coef);
 
 static thread_local char g_err[512] = "";
@@ -562,6 +564,8 @@ void ph_free(void *handle)
         mlp_free(static_cast<ph_mlp *>(handle));
     } else if (kind == KIND_GRAPH) {
         graph_free(static_cast<ph_graph *>(handle));
+    } else if (kind == KIND_PM) {
+        pm_free(static_cast<ph_pm *>(handle));
     }
 }
 
@@ -579,6 +583,7 @@ int ph_status(const void *handle)
         const ph_pairs *h = static_cast<const ph_pairs *>(handle);
         return read_status(h->status, h->last_stream);
     }
+    if (kind == KIND_PM) return pm_status(static_cast<const ph_pm *>(handle));
     if (kind == KIND_MLP || kind == KIND_GRAPH) return PH_OK;
     return fail(PH_ERR_STATE, "unknown handle");
 }

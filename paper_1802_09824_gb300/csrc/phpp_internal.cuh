@@ -100,6 +100,7 @@ enum HandleKind : uint32_t {
     KIND_PAIRS = 0x50414952u,
     KIND_MLP = 0x4d4c5021u,
     KIND_GRAPH = 0x47524150u,
+    KIND_PM = 0x504d2121u,
 };
 
 struct DevBuf {

@@ -1,0 +1,492 @@
+// Long-range side of the force split: the particle-mesh (PM) part of
+// Sec. 3.1 on one periodic box.
+//
+//   1. CIC assignment of the masses to an N^3 mesh (k_pm_deposit): 64-bit
+//      fixed-point atomics, so the node masses do not depend on the order of
+//      the additions (replays are bit-identical).
+//   2. FFT of the node masses (cuFFT, real to complex, FP32).
+//   3. Green's function of the 3-point difference Laplacian (the equation of
+//      Sec. 3.1), phi_k = -pi G Delta_g^2 rho_k / (sin^2(pi l/N) +
+//      sin^2(pi m/N) + sin^2(pi n/N)), times the long-range filter
+//      exp(-k^2 R_s^2) (the k-space complement of Eq. (split)); k = 0
+//      dropped (k_pm_green).
+//   4. Inverse FFT: the potential on the mesh.
+//   5. Mesh acceleration by the 2-point central difference (k_pm_grad), CIC
+//      interpolation back to the particles with the assignment weights
+//      (k_pm_interp), written or added to the caller's acceleration array.
+//
+// The cell of a particle is decided in FP64 with fixed roundings:
+// x_w = x - L floor(x / L) (x_w = L maps to 0), u = x_w (N / L),
+// i0 = floor(u) mod N, fraction u - floor(u).
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "phpp_internal.cuh"
+
+struct ph_pm {
+    uint32_t kind = phpp::KIND_PM;
+    cudaStream_t last_stream = nullptr;
+    int32_t n_mesh = 0;
+    int64_t last_n = 0;
+    bool plans = false;
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+    phpp::DevBuf mesh_q;     // unsigned long long [N^3]: node masses, fixed point
+    phpp::DevBuf mesh_r;     // float [N^3]: node masses, then the potential
+    phpp::DevBuf mesh_c;     // cufftComplex [N N (N/2+1)]
+    phpp::DevBuf mesh_a;     // float4 [N^3]: -grad phi (x, y, z) and phi
+    phpp::DevBuf tab;        // float [2N]: sin^2(pi l / N), exp(-k_l^2 R_s^2)
+    phpp::DevBuf fft_work;   // cuFFT work area (both plans)
+    phpp::DevBuf scale;      // uint32 largest |m| (float bits)
+    phpp::DevBuf status;     // uint32 device status word
+    phpp::DevBuf in_pos, in_mass, acc_tmp, pot_tmp;
+    double tab_L = 0.0, tab_rs = -1.0;
+};
+
+namespace phpp {
+
+namespace {
+
+constexpr int kPmThreads = 256;
+
+inline int grid_of(int64_t n, int per_block = kPmThreads)
+{
+    int64_t b = (n + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    if (b > cap) b = cap;
+    return (int)(b > 0 ? b : 1);
+}
+
+// Node and fraction of one coordinate (FP64, fixed roundings).
+__device__ __forceinline__ int pm_cell(double x, double L, double inv_dg, int N, double &f)
+{
+    const double q = floor(__ddiv_rn(x, L));
+    double xw = __dsub_rn(x, __dmul_rn(L, q));
+    if (xw >= L) xw = 0.0;
+    const double u = __dmul_rn(xw, inv_dg);
+    const double fl = floor(u);
+    f = __dsub_rn(u, fl);
+    // fl is in [-1, N]: -1 when x sits just below a multiple of L and x / L
+    // rounded up (then x_w is a tiny negative number), N when u rounded up
+    int i = (int)fl;
+    if (i >= N) i -= N;
+    if (i < 0) i += N;
+    return i;
+}
+
+template <int PT>
+__device__ __forceinline__ double load_coord(const void *pos, int64_t k)
+{
+    if (PT == PH_F64) return static_cast<const double *>(pos)[k];
+    return (double)static_cast<const float *>(pos)[k];
+}
+
+// Fixed-point scale 2^(62 - e) with n max|m| < 2^e: no node (nor the total)
+// can exceed 2^62 in magnitude.
+__device__ __forceinline__ double pm_scale(const uint32_t *mmax_bits, int64_t n)
+{
+    const double b = (double)__uint_as_float(*mmax_bits) * (double)n;
+    if (!(b > 0.0)) return 1.0;
+    return ldexp(1.0, 62 - (ilogb(b) + 1));
+}
+
+__global__ void k_pm_mass_max(const float *mass, int64_t n, float mass_default, uint32_t *mmax_bits,
+                              uint32_t *status)
+{
+    uint32_t best = 0;
+    if (!mass) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(mmax_bits, __float_as_uint(fabsf(mass_default)));
+        return;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float m = mass[i];
+        if (!isfinite(m)) {
+            atomicOr(status, ST_NONFINITE);
+            continue;
+        }
+        best = max(best, __float_as_uint(fabsf(m)));
+    }
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(mmax_bits, best);
+}
+
+template <int PT>
+__global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, float mass_default, double L,
+                             double inv_dg, int N, const uint32_t *mmax_bits, unsigned long long *mesh_q,
+                             uint32_t *status)
+{
+    const double S = pm_scale(mmax_bits, n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = load_coord<PT>(pos, 3 * i), y = load_coord<PT>(pos, 3 * i + 1),
+                     z = load_coord<PT>(pos, 3 * i + 2);
+        const double m = mass ? (double)mass[i] : (double)mass_default;
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(m))) {
+            atomicOr(status, ST_NONFINITE);
+            continue;
+        }
+        double fx, fy, fz;
+        const int ix = pm_cell(x, L, inv_dg, N, fx);
+        const int iy = pm_cell(y, L, inv_dg, N, fy);
+        const int iz = pm_cell(z, L, inv_dg, N, fz);
+        const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+        const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
+        const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
+        const int jz[2] = {iz, iz + 1 == N ? 0 : iz + 1};
+        const double mS = m * S;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const double wab = wx[a] * wy[b];
+                const int64_t row = ((int64_t)jx[a] * N + jy[b]) * N;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const long long q = __double2ll_rn(wab * wz[c] * mS);
+                    if (q) atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
+                }
+            }
+    }
+}
+
+// Node masses back to FP32 (the FFT input).
+__global__ void k_pm_unfix(const unsigned long long *mesh_q, int64_t cells, int64_t n, const uint32_t *mmax_bits,
+                           float *mesh_r)
+{
+    const double inv = 1.0 / pm_scale(mmax_bits, n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
+        mesh_r[i] = (float)((double)(long long)mesh_q[i] * inv);
+}
+
+// Multiply the half spectrum by the filtered Green's function.  c0 folds
+// -pi G Delta_g^2, the 1 / Delta_g^3 of the density and the 1 / N^3 of the
+// unnormalised inverse transform.
+__global__ void k_pm_green(float2 *mc, int N, const float *s2, const float *ek, float c0)
+{
+    const int nh = N / 2 + 1;
+    const int64_t total = (int64_t)N * N * nh;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % nh);
+        const int64_t r = idx / nh;
+        const int b = (int)(r % N);
+        const int a = (int)(r / N);
+        const float den = s2[a] + s2[b] + s2[c];
+        const float g = idx == 0 ? 0.f : c0 * (ek[a] * ek[b] * ek[c]) / den;
+        float2 v = mc[idx];
+        v.x *= g;
+        v.y *= g;
+        mc[idx] = v;
+    }
+}
+
+// -grad phi by the 2-point central difference; phi kept in w.
+__global__ void k_pm_grad(const float *phi, int N, float c_half, float4 *mesh_a)
+{
+    const int64_t cells = (int64_t)N * N * N;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < cells;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int64_t r = idx / N;
+        const int j = (int)(r % N);
+        const int i = (int)(r / N);
+        const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
+        const int jp = j + 1 == N ? 0 : j + 1, jm = j == 0 ? N - 1 : j - 1;
+        const int kp = k + 1 == N ? 0 : k + 1, km = k == 0 ? N - 1 : k - 1;
+        const int64_t NN = (int64_t)N * N;
+        float4 o;
+        o.x = c_half * (phi[ip * NN + (int64_t)j * N + k] - phi[im * NN + (int64_t)j * N + k]);
+        o.y = c_half * (phi[i * NN + (int64_t)jp * N + k] - phi[i * NN + (int64_t)jm * N + k]);
+        o.z = c_half * (phi[r * N + kp] - phi[r * N + km]);
+        o.w = phi[idx];
+        mesh_a[idx] = o;
+    }
+}
+
+template <int PT>
+__global__ void k_pm_interp(const void *pos, int64_t n, double L, double inv_dg, int N, const float4 *mesh_a,
+                            float *acc, float *pot, int accumulate)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = load_coord<PT>(pos, 3 * i), y = load_coord<PT>(pos, 3 * i + 1),
+                     z = load_coord<PT>(pos, 3 * i + 2);
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) continue;   // latched by the deposit
+        double fx, fy, fz;
+        const int ix = pm_cell(x, L, inv_dg, N, fx);
+        const int iy = pm_cell(y, L, inv_dg, N, fy);
+        const int iz = pm_cell(z, L, inv_dg, N, fz);
+        const float wx[2] = {(float)(1.0 - fx), (float)fx}, wy[2] = {(float)(1.0 - fy), (float)fy},
+                    wz[2] = {(float)(1.0 - fz), (float)fz};
+        const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
+        const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
+        const int jz[2] = {iz, iz + 1 == N ? 0 : iz + 1};
+        float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const float wab = wx[a] * wy[b];
+                const int64_t row = ((int64_t)jx[a] * N + jy[b]) * N;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const float w = wab * wz[c];
+                    const float4 v = __ldg(mesh_a + row + jz[c]);
+                    ax = fmaf(w, v.x, ax);
+                    ay = fmaf(w, v.y, ay);
+                    az = fmaf(w, v.z, az);
+                    ph = fmaf(w, v.w, ph);
+                }
+            }
+        if (accumulate) {
+            acc[3 * i] += ax;
+            acc[3 * i + 1] += ay;
+            acc[3 * i + 2] += az;
+        } else {
+            acc[3 * i] = ax;
+            acc[3 * i + 1] = ay;
+            acc[3 * i + 2] = az;
+        }
+        if (pot) pot[i] = ph;
+    }
+}
+
+int cufft_check(cufftResult r, const char *what)
+{
+    if (r == CUFFT_SUCCESS) return PH_OK;
+    if (r == CUFFT_ALLOC_FAILED) return fail(PH_ERR_OOM, "%s: cuFFT allocation failed", what);
+    return fail(PH_ERR_CUDA, "%s: cuFFT error %d", what, (int)r);
+}
+
+void pm_release(ph_pm *h)
+{
+    if (h->plans) {
+        cufftDestroy(h->plan_r2c);
+        cufftDestroy(h->plan_c2r);
+        h->plans = false;
+    }
+    DevBuf *bufs[] = {&h->mesh_q, &h->mesh_r, &h->mesh_c, &h->mesh_a, &h->tab, &h->fft_work, &h->scale,
+                      &h->status, &h->in_pos, &h->in_mass, &h->acc_tmp, &h->pot_tmp};
+    for (DevBuf *b : bufs) release(*b);
+}
+
+// Mesh buffers and FFT plans for an N^3 mesh (kept while N is unchanged).
+int pm_setup(ph_pm *h, int N)
+{
+    if (h->plans && h->n_mesh == N) return PH_OK;
+    if (h->plans) {
+        cufftDestroy(h->plan_r2c);
+        cufftDestroy(h->plan_c2r);
+        h->plans = false;
+    }
+    const size_t cells = (size_t)N * N * N, half = (size_t)N * N * (N / 2 + 1);
+    int rc = ensure(h->mesh_q, 8 * cells);
+    if (!rc) rc = ensure(h->mesh_r, 4 * cells);
+    if (!rc) rc = ensure(h->mesh_c, 8 * half);
+    if (!rc) rc = ensure(h->mesh_a, 16 * cells);
+    if (!rc) rc = ensure(h->tab, 8 * (size_t)N);
+    if (!rc) rc = ensure(h->scale, 16);
+    if (rc) return rc;
+    size_t w1 = 0, w2 = 0;
+    rc = cufft_check(cufftCreate(&h->plan_r2c), "cufftCreate");
+    if (rc) return rc;
+    if ((rc = cufft_check(cufftCreate(&h->plan_c2r), "cufftCreate"))) {
+        cufftDestroy(h->plan_r2c);
+        return rc;
+    }
+    h->plans = true;
+    rc = cufft_check(cufftSetAutoAllocation(h->plan_r2c, 0), "cufftSetAutoAllocation");
+    if (!rc) rc = cufft_check(cufftSetAutoAllocation(h->plan_c2r, 0), "cufftSetAutoAllocation");
+    if (!rc) rc = cufft_check(cufftMakePlan3d(h->plan_r2c, N, N, N, CUFFT_R2C, &w1), "cufftMakePlan3d R2C");
+    if (!rc) rc = cufft_check(cufftMakePlan3d(h->plan_c2r, N, N, N, CUFFT_C2R, &w2), "cufftMakePlan3d C2R");
+    if (!rc) rc = ensure(h->fft_work, std::max<size_t>(std::max(w1, w2), 16));
+    if (!rc) rc = cufft_check(cufftSetWorkArea(h->plan_r2c, h->fft_work.p), "cufftSetWorkArea");
+    if (!rc) rc = cufft_check(cufftSetWorkArea(h->plan_c2r, h->fft_work.p), "cufftSetWorkArea");
+    if (rc) {
+        cufftDestroy(h->plan_r2c);
+        cufftDestroy(h->plan_c2r);
+        h->plans = false;
+        return rc;
+    }
+    h->n_mesh = N;
+    h->tab_rs = -1.0;
+    return PH_OK;
+}
+
+// The per-axis factors of the Green's function: sin^2(pi l / N) and
+// exp(-(2 pi l' / L)^2 R_s^2) with l' the signed frequency, in FP64 on the
+// host, rounded to FP32; uploaded when N, L or R_s change.
+int pm_tables(ph_pm *h, double L, double rs, cudaStream_t s)
+{
+    if (h->tab_L == L && h->tab_rs == rs) return PH_OK;
+    const int N = h->n_mesh;
+    std::vector<float> t(2 * (size_t)N);
+    for (int l = 0; l < N; l++) {
+        const double sn = std::sin(M_PI * l / N);
+        t[l] = (float)(sn * sn);
+        const int ls = l > N / 2 ? l - N : l;
+        const double k = 2.0 * M_PI * ls / L;
+        t[N + l] = (float)std::exp(-k * k * rs * rs);
+    }
+    int rc = cuda_check(cudaStreamSynchronize(s), "sync before table upload");
+    if (!rc) rc = cuda_check(cudaMemcpy(h->tab.p, t.data(), t.size() * 4, cudaMemcpyHostToDevice), "upload PM tables");
+    if (rc) return rc;
+    h->tab_L = L;
+    h->tab_rs = rs;
+    return PH_OK;
+}
+
+}  // namespace
+
+void pm_free(ph_pm *h)
+{
+    pm_release(h);
+    delete h;
+}
+
+int pm_status(const ph_pm *h)
+{
+    uint32_t st = 0;
+    int rc = cuda_check(cudaMemcpyAsync(&st, h->status.p, 4, cudaMemcpyDeviceToHost, h->last_stream), "read status");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->last_stream), "status sync");
+    if (rc) return rc;
+    if (st & ST_NONFINITE) return fail(PH_ERR_NONFINITE, "non-finite position or mass");
+    return PH_OK;
+}
+
+}  // namespace phpp
+
+using namespace phpp;
+
+extern "C" {
+
+int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params,
+                int32_t n_mesh, float *acc, float *pot, int32_t accumulate, void *stream, ph_pm **pm)
+{
+    if (!pm || !params) return fail(PH_ERR_ARG, "pm and params must not be NULL");
+    if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
+    if (n < 0 || n >= (int64_t)1 << 31) return fail(PH_ERR_ARG, "n must be 0..2^31-1");
+    if (n > 0 && (!pos || !acc)) return fail(PH_ERR_ARG, "pos and acc must not be NULL");
+    if (n_mesh < 4 || n_mesh > PH_PM_MAX_MESH || (n_mesh & 1))
+        return fail(PH_ERR_ARG, "n_mesh must be even and in 4..%d", PH_PM_MAX_MESH);
+    const ph_params &p = *params;
+    if (!(std::isfinite(p.L) && p.L > 0)) return fail(PH_ERR_ARG, "L must be finite and > 0");
+    if (!(std::isfinite(p.rs) && p.rs >= 0)) return fail(PH_ERR_ARG, "rs must be >= 0");
+    if (!std::isfinite(p.G)) return fail(PH_ERR_ARG, "G must be finite");
+    ph_pm *h = *pm;
+    if (h && h->kind != KIND_PM) return fail(PH_ERR_STATE, "handle is not a ph_pm");
+    const bool fresh = !h;
+    if (fresh) {
+        h = new (std::nothrow) ph_pm();
+        if (!h) return fail(PH_ERR_OOM, "host allocation failed");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    int rc = ensure(h->status, 16);
+    if (!rc && fresh) rc = cuda_check(cudaMemsetAsync(h->status.p, 0, 16, s), "status reset");
+    if (!rc) rc = pm_setup(h, n_mesh);
+    if (!rc) rc = pm_tables(h, p.L, p.rs, s);
+    if (rc) {
+        if (fresh) pm_free(h);
+        return rc;
+    }
+    *pm = h;
+    h->last_n = n;
+    if (n == 0) return PH_OK;
+
+    // inputs and outputs in host memory go through device copies
+    const void *dpos = pos;
+    const float *dmass = mass;
+    float *dacc = acc, *dpot = pot;
+    const bool host_acc = !is_device_ptr(acc), host_pot = pot && !is_device_ptr(pot);
+    const size_t pbytes = (size_t)n * 3 * (pos_type == PH_F64 ? 8 : 4);
+    if (!is_device_ptr(pos)) {
+        rc = ensure(h->in_pos, pbytes);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(h->in_pos.p, pos, pbytes, cudaMemcpyHostToDevice, s), "copy positions");
+        dpos = h->in_pos.p;
+    }
+    if (!rc && mass && !is_device_ptr(mass)) {
+        rc = ensure(h->in_mass, (size_t)n * 4);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(h->in_mass.p, mass, (size_t)n * 4, cudaMemcpyHostToDevice, s),
+                                 "copy masses");
+        dmass = static_cast<const float *>(h->in_mass.p);
+    }
+    if (!rc && host_acc) {
+        rc = ensure(h->acc_tmp, (size_t)n * 12);
+        dacc = static_cast<float *>(h->acc_tmp.p);
+        if (!rc && accumulate)
+            rc = cuda_check(cudaMemcpyAsync(dacc, acc, (size_t)n * 12, cudaMemcpyHostToDevice, s), "copy acc in");
+    }
+    if (!rc && host_pot) {
+        rc = ensure(h->pot_tmp, (size_t)n * 4);
+        dpot = static_cast<float *>(h->pot_tmp.p);
+    }
+    if (rc) return rc;
+
+    const int N = n_mesh;
+    const int64_t cells = (int64_t)N * N * N;
+    const double dg = p.L / N, inv_dg = (double)N / p.L;
+    const float mdef = (float)(1.0 / (double)n);
+    uint32_t *st = static_cast<uint32_t *>(h->status.p);
+    uint32_t *mmax = static_cast<uint32_t *>(h->scale.p);
+    unsigned long long *mq = static_cast<unsigned long long *>(h->mesh_q.p);
+    rc = cuda_check(cudaMemsetAsync(mmax, 0, 4, s), "clear scale");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(mq, 0, 8 * (size_t)cells, s), "clear mesh");
+    if (rc) return rc;
+    k_pm_mass_max<<<dmass ? grid_of(n) : 1, kPmThreads, 0, s>>>(dmass, n, mdef, mmax, st);
+    if (pos_type == PH_F64)
+        k_pm_deposit<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, N, mmax, mq, st);
+    else
+        k_pm_deposit<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, N, mmax, mq, st);
+    float *mr = static_cast<float *>(h->mesh_r.p);
+    k_pm_unfix<<<grid_of(cells), kPmThreads, 0, s>>>(mq, cells, n, mmax, mr);
+    count_launch(3);
+    rc = cufft_check(cufftSetStream(h->plan_r2c, s), "cufftSetStream");
+    if (!rc) rc = cufft_check(cufftSetStream(h->plan_c2r, s), "cufftSetStream");
+    if (!rc) rc = cufft_check(cufftExecR2C(h->plan_r2c, mr, static_cast<cufftComplex *>(h->mesh_c.p)), "R2C");
+    if (rc) return rc;
+    const float *s2 = static_cast<const float *>(h->tab.p);
+    const double c0 = -M_PI * p.G / (dg * (double)cells);
+    k_pm_green<<<grid_of((int64_t)N * N * (N / 2 + 1)), kPmThreads, 0, s>>>(static_cast<float2 *>(h->mesh_c.p), N, s2,
+                                                                          s2 + N, (float)c0);
+    count_launch();
+    rc = cufft_check(cufftExecC2R(h->plan_c2r, static_cast<cufftComplex *>(h->mesh_c.p), mr), "C2R");
+    if (rc) return rc;
+    float4 *ma = static_cast<float4 *>(h->mesh_a.p);
+    k_pm_grad<<<grid_of(cells), kPmThreads, 0, s>>>(mr, N, (float)(-0.5 / dg), ma);
+    if (pos_type == PH_F64)
+        k_pm_interp<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate);
+    else
+        k_pm_interp<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate);
+    count_launch(2);
+    rc = cuda_check(cudaGetLastError(), "PM kernels");
+    if (!rc && host_acc)
+        rc = cuda_check(cudaMemcpyAsync(acc, dacc, (size_t)n * 12, cudaMemcpyDeviceToHost, s), "copy acc out");
+    if (!rc && host_pot)
+        rc = cuda_check(cudaMemcpyAsync(pot, dpot, (size_t)n * 4, cudaMemcpyDeviceToHost, s), "copy pot out");
+    if (!rc && (host_acc || host_pot)) rc = cuda_check(cudaStreamSynchronize(s), "PM sync");
+    return rc;
+}
+
+int ph_pm_get_view(const ph_pm *pm, ph_pm_view *out)
+{
+    if (!pm || pm->kind != KIND_PM || !out) return fail(PH_ERR_ARG, "bad arguments");
+    int rc = cuda_check(cudaStreamSynchronize(pm->last_stream), "view sync");
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    uint32_t bits = 0;
+    rc = cuda_check(cudaMemcpy(&bits, pm->scale.p, 4, cudaMemcpyDeviceToHost), "read scale");
+    if (rc) return rc;
+    float mmax = 0.f;
+    memcpy(&mmax, &bits, 4);
+    const double b = (double)mmax * (double)pm->last_n;
+    out->n_mesh = pm->n_mesh;
+    out->mass_unit = b > 0.0 ? std::ldexp(1.0, std::ilogb(b) + 1 - 62) : 1.0;
+    out->mass_fixed = static_cast<const int64_t *>(pm->mesh_q.p);
+    out->mesh = static_cast<const float *>(pm->mesh_a.p);
+    return PH_OK;
+}
+
+}  // extern "C"
