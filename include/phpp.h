@@ -273,8 +273,9 @@ int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int6
  *   5. a = -grad phi on the mesh by the 2-point central difference, then
  *      Cloud-in-Cell interpolation to each particle with the assignment
  *      weights.  No window deconvolution.
- * The cell of a particle is decided in FP64: x_w = x - L floor(x/L),
- * u = x_w (N/L), node floor(u) mod N, fraction u - floor(u).
+ * The cell of a particle is decided in FP64: a coordinate in [0, L) is kept,
+ * any other becomes x_w = x - L floor(x/L); u = x_w (N/L), node floor(u)
+ * mod N, fraction u - floor(u).
  *
  *   pos, pos_type, mass, n   as for ph_build_leaves (host or device; mass
  *                NULL = 1/n each); one box, caller order.

@@ -34,8 +34,9 @@ Readings taken here (the paper is silent or garbled on each):
   particle with the assignment weights (so momentum is conserved).
 * No deconvolution of the CIC window (the paper mentions none).
 * The cell index of a particle is an integer decided by floating point: it
-  is taken in FP64 with fixed operations (x - L floor(x / L), then
-  u = x_w * (N / L), i0 = floor(u)), the same ones the CUDA path uses.
+  is taken in FP64 with fixed operations (a coordinate in [0, L) is used
+  as it is, any other becomes x - L floor(x / L); then u = x_w * (N / L),
+  i0 = floor(u)), the same ones the CUDA path uses.
 """
 from __future__ import annotations
 
@@ -45,11 +46,12 @@ import numpy as np
 def cic_cells(pos, L, n_mesh):
     """Lower CIC node (int64 [P,3]) and fractional offset (float64 [P,3]).
 
-    x is wrapped into [0, L) as x - L floor(x / L) (L itself maps to 0), then
-    u = x * (N / L) in mesh units; node i0 = floor(u) mod N, fraction
-    u - floor(u)."""
+    A coordinate already in [0, L) is kept; any other is wrapped as
+    x - L floor(x / L) (a result equal to L maps to 0).  Then u = x * (N / L)
+    in mesh units; node i0 = floor(u) mod N, fraction u - floor(u)."""
     x = np.asarray(pos, np.float64)
-    xw = x - L * np.floor(x / L)
+    inside = (x >= 0.0) & (x < L)
+    xw = np.where(inside, x, x - L * np.floor(x / L))
     xw = np.where(xw >= L, 0.0, xw)
     u = xw * (n_mesh / L)
     fl = np.floor(u)

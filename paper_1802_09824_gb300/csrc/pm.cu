@@ -15,9 +15,10 @@
 //      interpolation back to the particles with the assignment weights
 //      (k_pm_interp), written or added to the caller's acceleration array.
 //
-// The cell of a particle is decided in FP64 with fixed roundings:
-// x_w = x - L floor(x / L) (x_w = L maps to 0), u = x_w (N / L),
-// i0 = floor(u) mod N, fraction u - floor(u).
+// The cell of a particle is decided in FP64 with fixed roundings: a
+// coordinate in [0, L) is kept, any other becomes x_w = x - L floor(x / L)
+// (x_w = L maps to 0); u = x_w (N / L), i0 = floor(u) mod N, fraction
+// u - floor(u).
 #include <cufft.h>
 
 #include <algorithm>
@@ -61,12 +62,17 @@ inline int grid_of(int64_t n, int per_block = kPmThreads)
     return (int)(b > 0 ? b : 1);
 }
 
-// Node and fraction of one coordinate (FP64, fixed roundings).
+// Node and fraction of one coordinate (FP64, fixed roundings).  The FP64
+// division of the wrap (a long instruction sequence on this GPU's narrow
+// FP64 pipe) is only taken for coordinates outside [0, L).
 __device__ __forceinline__ int pm_cell(double x, double L, double inv_dg, int N, double &f)
 {
-    const double q = floor(__ddiv_rn(x, L));
-    double xw = __dsub_rn(x, __dmul_rn(L, q));
-    if (xw >= L) xw = 0.0;
+    double xw = x;
+    if (!(x >= 0.0 && x < L)) {
+        const double q = floor(__ddiv_rn(x, L));
+        xw = __dsub_rn(x, __dmul_rn(L, q));
+        if (xw >= L) xw = 0.0;
+    }
     const double u = __dmul_rn(xw, inv_dg);
     const double fl = floor(u);
     f = __dsub_rn(u, fl);
@@ -137,6 +143,7 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
         const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
         const int jz[2] = {iz, iz + 1 == N ? 0 : iz + 1};
         const double mS = m * S;
+        const double wzm[2] = {wz[0] * mS, wz[1] * mS};
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
@@ -145,7 +152,7 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
                 const int64_t row = ((int64_t)jx[a] * N + jy[b]) * N;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const long long q = __double2ll_rn(wab * wz[c] * mS);
+                    const long long q = __double2ll_rn(wab * wzm[c]);
                     if (q) atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
                 }
             }
