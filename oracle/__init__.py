@@ -18,4 +18,6 @@ Modules:
   pm      -- the long-range particle-mesh side (CIC, Green's function of
              the 3-point difference Laplacian with the split filter, central
              difference, CIC interpolation), numpy float64
+  kdk     -- adaptive Kick-Drift-Kick block steps under the split force
+             (Newtonian or flat Lambda-CDM drift/kick factors)
 """
