@@ -124,6 +124,7 @@ typedef struct ph_pairs  ph_pairs;    /* cutoff leaf-pair list (CSR by group)   
 typedef struct ph_mlp    ph_mlp;      /* learned short-range factor             */
 typedef struct ph_graph  ph_graph;    /* a whole step captured as a CUDA graph  */
 typedef struct ph_pm     ph_pm;       /* long-range particle-mesh solver         */
+typedef struct ph_sim    ph_sim;      /* particles advanced by adaptive KDK steps */
 
 /*
  * Sort the particles of one box along the space-filling curve and cut them
@@ -313,7 +314,65 @@ typedef struct ph_pm_view {
 /* Device views of the last ph_pm_accel's meshes (synchronises). */
 int ph_pm_get_view(const ph_pm *pm, ph_pm_view *out);
 
-/* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph, ph_pm).  NULL is a no-op. */
+/* ------------------------------------------------------------ adaptive KDK
+ * The time integration of Sec. 3.5 driving repeated force calls: the
+ * symplectic Drift x += p int dt/a^2 and Kick p += a_grav int dt/a, applied
+ * as Kick-Drift-Kick, with every particle's step the top step halved until
+ * it is below t_acc = sqrt(2 eta eps / |a|) (Gadget-2's criterion; the
+ * printed form is garbled), so steps are dt / 2^level and meet at the ends
+ * of coarser steps (block steps).
+ *
+ * One top step: every particle takes its level from its acceleration and an
+ * opening half kick; then, at each event (the earliest end of any
+ * particle's current step, on a timeline of 2^max_level ticks), all
+ * particles drift to it, the force is recomputed for all (ph_accel: build,
+ * pairs, short-range PP; then ph_pm_accel added when n_mesh > 0), the
+ * particles whose step ends take their closing half kick and, before the
+ * top step's end, a new level (refined until its step length divides the
+ * elapsed ticks) and an opening half kick.  The level is the smallest k in
+ * [0, max_level] with (dt_phys / 2^k)^2 |a| <= 2 eta eps_step, decided in
+ * FP64.  Positions (FP64) stay in [0, L).
+ *
+ * Clocks: PH_CLOCK_NEWTON (time t, drift and kick factors t2 - t1) or
+ * PH_CLOCK_LCDM (time = scale factor a of a flat Lambda-CDM universe,
+ * D = int da / (a^3 H), K = int da / (a^2 H), H = H0 sqrt(omega_m a^-3 +
+ * omega_l); dt_phys = dt / (a H(a)) in the criterion).
+ */
+#define PH_CLOCK_NEWTON 0
+#define PH_CLOCK_LCDM   1
+
+typedef struct ph_kdk_params {
+    double  dt;         /* top step in the time variable (> 0)                  */
+    double  eta;        /* accuracy parameter of the criterion (> 0)            */
+    double  eps_step;   /* softening length of the criterion; 0 = params->eps   */
+    double  H0, omega_m, omega_l;   /* PH_CLOCK_LCDM only                       */
+    int32_t max_level;  /* finest level, 0..20 (steps down to dt / 2^max_level) */
+    int32_t n_mesh;     /* PM mesh for the long-range force; 0 = short range only */
+    int32_t clock;      /* PH_CLOCK_NEWTON or PH_CLOCK_LCDM                     */
+    int32_t g_mode;     /* PH_G_EXACT or PH_G_TABLE                             */
+} ph_kdk_params;
+
+/*
+ * Copy n particles (pos, mom [n*3] float64, mass [n] float32 or NULL = 1/n;
+ * host or device) into a new simulation at time t0 (for PH_CLOCK_LCDM the
+ * scale factor a0 > 0), wrap the positions into [0, L) and compute their
+ * first force.  params: the box of ph_build_leaves.  *sim must be NULL.
+ * Synchronises.
+ */
+int ph_sim_create(const double *pos, const double *mom, const float *mass, int64_t n, const ph_params *params,
+                  const ph_kdk_params *kp, double t0, void *stream, ph_sim **sim);
+
+/* Advance by n_steps top steps (one host synchronisation per event). */
+int ph_sim_step(ph_sim *sim, int32_t n_steps, void *stream);
+
+/* Current state (each output host or device, nullable): positions and
+ * momenta [n*3] float64, last accelerations [n*3] float32, levels [n] of
+ * the last top step, time, and force passes so far.  Synchronises and
+ * reports any status latched by the force calls. */
+int ph_sim_get(const ph_sim *sim, double *pos, double *mom, float *acc, int32_t *level, double *t,
+               int64_t *force_passes);
+
+/* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph, ph_pm, ph_sim).  NULL is a no-op. */
 void ph_free(void *handle);
 
 /* Message of the last failing call on this thread ("" if none). */

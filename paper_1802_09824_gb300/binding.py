@@ -84,6 +84,14 @@ class ph_pm_view(ctypes.Structure):
 
 
 PH_PM_MAX_MESH = 1024
+PH_CLOCK_NEWTON, PH_CLOCK_LCDM = 0, 1
+
+
+class ph_kdk_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("eta", ctypes.c_double), ("eps_step", ctypes.c_double),
+                ("H0", ctypes.c_double), ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
+                ("max_level", ctypes.c_int32), ("n_mesh", ctypes.c_int32), ("clock", ctypes.c_int32),
+                ("g_mode", ctypes.c_int32)]
 
 _lib = None
 
@@ -120,6 +128,11 @@ _SIGS = {
     "ph_pm_accel": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.c_int32, _VP, _VP,
                      ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_pm_get_view": ([_VP, ctypes.POINTER(ph_pm_view)], ctypes.c_int),
+    "ph_sim_create": ([_VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.POINTER(ph_kdk_params),
+                       ctypes.c_double, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_sim_step": ([_VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "ph_sim_get": ([_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+                   ctypes.c_int),
     "ph_autotune": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(ph_params),
                      ctypes.c_int32, _VP, ctypes.POINTER(ph_tune_result)], ctypes.c_int),
 }
@@ -399,6 +412,38 @@ def ph_pm_get_view(pm):
     return {"n_mesh": n, "mass_unit": v.mass_unit,
             "mass_fixed": _dev(v.mass_fixed, (n, n, n), "<i8"),
             "mesh": _dev(v.mesh, (n, n, n, 4), "<f4")}
+
+
+def make_kdk_params(dt, eta, max_level, n_mesh=0, eps_step=0.0, clock=PH_CLOCK_NEWTON, H0=1.0, omega_m=1.0,
+                    omega_l=0.0, g_mode=PH_G_EXACT):
+    return ph_kdk_params(float(dt), float(eta), float(eps_step), float(H0), float(omega_m), float(omega_l),
+                         int(max_level), int(n_mesh), int(clock), int(g_mode))
+
+
+def ph_sim_create(pos, mom, mass, params, kp, t0=0.0, stream=None):
+    """New simulation from float64 positions/momenta [N,3] and float32 masses
+    (host or device tensors / arrays; mass None = 1/N)."""
+    out = ctypes.c_void_p(None)
+    _check(lib().ph_sim_create(_ptr(pos), _ptr(mom), _ptr(mass), int(pos.shape[0]), ctypes.byref(params),
+                               ctypes.byref(kp), float(t0), _stream(stream), ctypes.byref(out)))
+    return Handle(out.value)
+
+
+def ph_sim_step(sim, n_steps=1, stream=None):
+    return _check(lib().ph_sim_step(sim.ptr, int(n_steps), _stream(stream)))
+
+
+def ph_sim_get(sim, n):
+    """(positions float64 [N,3], momenta float64 [N,3], accelerations float32
+    [N,3], levels int32 [N], time, force passes) as numpy arrays."""
+    x = np.zeros((n, 3))
+    p = np.zeros((n, 3))
+    a = np.zeros((n, 3), np.float32)
+    lv = np.zeros(n, np.int32)
+    t = ctypes.c_double(0)
+    fp = ctypes.c_int64(0)
+    _check(lib().ph_sim_get(sim.ptr, _ptr(x), _ptr(p), _ptr(a), _ptr(lv), ctypes.byref(t), ctypes.byref(fp)))
+    return x, p, a, lv, t.value, fp.value
 
 
 def ph_launch_counter():

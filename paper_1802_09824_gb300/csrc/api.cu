@@ -57,6 +57,7 @@ int ensure_table(ph_leaves *lv, cudaStream_t s)
 void graph_free(ph_graph *g);
 void pm_free(ph_pm *h);
 int pm_status(const ph_pm *h);
+void sim_free(ph_sim *h);
 void fit_factor_poly(double U, int deg, float *coef);
 
 static thread_local char g_err[512] = "";
@@ -566,6 +567,8 @@ void ph_free(void *handle)
         graph_free(static_cast<ph_graph *>(handle));
     } else if (kind == KIND_PM) {
         pm_free(static_cast<ph_pm *>(handle));
+    } else if (kind == KIND_SIM) {
+        sim_free(static_cast<ph_sim *>(handle));
     }
 }
 
@@ -584,6 +587,8 @@ int ph_status(const void *handle)
         return read_status(h->status, h->last_stream);
     }
     if (kind == KIND_PM) return pm_status(static_cast<const ph_pm *>(handle));
+    if (kind == KIND_SIM) return ph_sim_get(static_cast<const ph_sim *>(handle), nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, nullptr);
     if (kind == KIND_MLP || kind == KIND_GRAPH) return PH_OK;
     return fail(PH_ERR_STATE, "unknown handle");
 }

@@ -101,6 +101,7 @@ enum HandleKind : uint32_t {
     KIND_MLP = 0x4d4c5021u,
     KIND_GRAPH = 0x47524150u,
     KIND_PM = 0x504d2121u,
+    KIND_SIM = 0x53494d21u,
 };
 
 struct DevBuf {

@@ -1,0 +1,148 @@
+"""Adaptive KDK block steps through the C ABI (ph_sim_*) against the FP64
+oracle integrator (oracle/kdk.py).
+
+The workload is a perturbed 16^3 lattice (slow particles, level 0) with four
+close binaries (fast particles, level 4 with the Newtonian clock): the two
+populations sit far from any level boundary, which the test checks on the
+oracle's decisions (the level is an integer decided from |a|, and the GPU's
+FP32 forces differ from the oracle's by up to 1e-3 relative; a decision
+within that of a boundary could go either way).
+
+Tolerances.  Every force pass carries the PP (p99 1e-5, max 1e-3) and PM
+(p99 2e-5, max 5e-4) relative errors; momenta change by sums of kicks of
+these forces, so their error relative to the change p - p0 is bounded by the
+same figures, and the positions' error relative to the displacement the
+kicks caused (x - x0 - p0 * total drift) likewise.  The gates allow 2.5x
+(p99) and 2x (max) of the sums."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kdk
+
+pytestmark = pytest.mark.gpu
+
+P99 = 7.5e-5
+EMAX = 3e-3
+
+
+def _system(seed=21):
+    rng = np.random.default_rng(seed)
+    ns, L = 16, 1.0
+    g = (np.arange(ns) + 0.5) / ns
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    pos += rng.normal(size=pos.shape) * 0.05 / ns
+    n0 = len(pos)
+    m = 1.0 / (n0 + 4)
+    mom = rng.normal(size=pos.shape) * 0.02
+    extra_x, extra_p = [], []
+    for k in rng.choice(n0, 4, replace=False):
+        sep = 0.004
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        w = np.cross(u, rng.normal(size=3))
+        w /= np.linalg.norm(w)
+        v = math.sqrt(2 * m / sep) / 2          # circular: each member at sep/2
+        extra_x.append(pos[k] + u * sep)
+        centre = mom[k].copy()
+        mom[k] = centre - w * v
+        extra_p.append(centre + w * v)
+    pos = np.concatenate([pos, np.array(extra_x)]) % L
+    mom = np.concatenate([mom, np.array(extra_p)])
+    mass = np.full(len(pos), m, np.float32)
+    return pos, mom, mass, L
+
+
+BOX = dict(G=1.0, eps=1e-3, rs=1.25 / 16, rcut=4.5 * 1.25 / 16)
+
+
+def _margins(monkeypatch, max_level):
+    rec = []
+    orig = kdk.step_levels
+
+    def spy(acc, dt, eta, eps, kmax):
+        a = np.asarray(acc, np.float64)
+        amag = np.sqrt(a[:, 0] ** 2 + a[:, 1] ** 2 + a[:, 2] ** 2)
+        r = dt * dt * amag / (2 * eta * eps)
+        mm = np.log(np.maximum(r, 1e-300)) / np.log(4.0)
+        d = np.where(mm <= 0, -mm, np.where(mm >= kmax, mm - kmax, np.minimum(mm - np.floor(mm), np.ceil(mm) - mm)))
+        rec.append(float(d.min()) if d.size else 1.0)
+        return orig(acc, dt, eta, eps, kmax)
+
+    monkeypatch.setattr(kdk, "step_levels", spy)
+    return rec
+
+
+def _rel(got, ref, base):
+    den = np.linalg.norm(ref - base, axis=1)
+    tau = 1e-3 * np.median(den)
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(den, tau)
+
+
+@pytest.mark.parametrize("clock", [kdk.CLOCK_NEWTON, kdk.CLOCK_LCDM])
+def test_kdk_matches_oracle(gpu_lib, monkeypatch, clock):
+    B = gpu_lib
+    pos, mom, mass, L = _system()
+    n = len(pos)
+    eta, max_level, n_mesh = 0.025, 5, 16
+    if clock == kdk.CLOCK_NEWTON:
+        dt, t0, ck = 0.0196, 0.0, kdk.Clock()
+        kp = B.make_kdk_params(dt, eta, max_level, n_mesh)
+    else:
+        # the top step in the scale factor whose physical length matches
+        # the Newtonian case at a = 0.5 (a H(a) = 0.88 for H0 = 1)
+        dt, t0 = 0.0196 * 0.5 * math.sqrt(0.3 / 0.125 + 0.7), 0.5
+        ck = kdk.Clock(kdk.CLOCK_LCDM, 1.0, 0.3, 0.7)
+        kp = B.make_kdk_params(dt, eta, max_level, n_mesh, clock=B.PH_CLOCK_LCDM, H0=1.0, omega_m=0.3,
+                               omega_l=0.7)
+    rec = _margins(monkeypatch, max_level)
+    ref = kdk.Sim(pos, mom, mass, L, BOX["G"], BOX["eps"], BOX["rs"], BOX["rcut"], n_mesh, dt, eta, max_level,
+                  t0=t0, clock=ck)
+    x0 = ref.x.copy()
+    for _ in range(2):
+        ref.top_step()
+    # every level decision of the oracle is at least 1% in |a| from a boundary
+    assert min(rec) > math.log(1.01) / math.log(4)
+    assert ref.level.min() == 0 and ref.level.max() >= 1
+
+    prm = B.make_params(L, BOX["G"], BOX["eps"], BOX["rs"], BOX["rcut"], 32)
+    sim = B.ph_sim_create(np.ascontiguousarray(pos), np.ascontiguousarray(mom), mass, prm, kp, t0)
+    B.ph_sim_step(sim, 2)
+    x, p, a, lv, t, fp = B.ph_sim_get(sim, n)
+    assert np.array_equal(lv, ref.level)
+    assert fp == ref.force_passes
+    assert abs(t - ref.t) <= 1e-15 * max(1.0, abs(ref.t))
+    # momenta against the change the kicks made
+    e = _rel(p, ref.p, mom)
+    assert np.percentile(e, 99) <= P99 and e.max() <= EMAX, (np.percentile(e, 99), e.max())
+    # positions (minimum image) against the displacement the kicks caused
+    drift = ck.drift(t0, ref.t)
+    d = x - ref.x
+    d -= L * np.round(d / L)
+    disp = ref.x - (x0 + mom * drift)
+    disp -= L * np.round(disp / L)
+    den = np.linalg.norm(disp, axis=1)
+    ex = np.linalg.norm(d, axis=1) / np.maximum(den, 1e-3 * np.median(den))
+    assert np.percentile(ex, 99) <= P99 and ex.max() <= EMAX, (np.percentile(ex, 99), ex.max())
+    B.ph_free(sim)
+
+
+def test_kdk_arguments(gpu_lib):
+    B = gpu_lib
+    pos = np.random.default_rng(0).random((64, 3))
+    mom = np.zeros((64, 3))
+    prm = B.make_params(1.0, 1.0, 1e-3, 0.04, 0.18, 32)
+    for kp in (B.make_kdk_params(0.0, 0.02, 2), B.make_kdk_params(0.01, 0.02, 21),
+               B.make_kdk_params(0.01, 0.02, 2, n_mesh=15),
+               B.make_kdk_params(0.01, 0.02, 2, clock=B.PH_CLOCK_LCDM, H0=0.0)):
+        with pytest.raises(B.PhError) as ei:
+            B.ph_sim_create(pos, mom, None, prm, kp, 0.0)
+        assert ei.value.code == B.PH_ERR_ARG
+    # a simulation with one level and no mesh runs plain KDK steps
+    sim = B.ph_sim_create(pos, mom, None, prm, B.make_kdk_params(0.001, 1e3, 0), 0.0)
+    B.ph_sim_step(sim, 3)
+    x, p, a, lv, t, fp = B.ph_sim_get(sim, 64)
+    assert fp == 4 and np.all(lv == 0) and abs(t - 0.003) < 1e-15
+    B.ph_free(sim)
