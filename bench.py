@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -291,6 +292,81 @@ def _tree_extra(B, stream, flush, theta=0.3):
     out["speedup_vs_theta0"] = out["theta0"]["step_ms"] / out["theta"]["step_ms"]
     out["oracle_targets"] = int(tg.size)
     return out
+
+
+def _pm_extra(B, ps, pos, mass, prm, graph, acc, stream, flush, n_mesh):
+    """The long-range PM side on the same particles (mesh n_mesh^3): its time
+    alone, the time of the whole split force (the captured short-range step
+    followed by PM added to its result), and its error against the FP64
+    oracle's PM on sampled targets."""
+    import torch
+    from oracle import pm as opm
+    bp = ps.boxes[0]
+    acc_pm = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
+    h = B.ph_pm_accel(pos, mass, prm, n_mesh, acc_pm, stream=stream)
+    for _ in range(3):
+        B.ph_pm_accel(pos, mass, prm, n_mesh, acc_pm, stream=stream, pm=h)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=7):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_pm = timed(lambda: B.ph_pm_accel(pos, mass, prm, n_mesh, acc_pm, stream=stream, pm=h))
+
+    def total():
+        B.ph_graph_launch(graph, stream)
+        B.ph_pm_accel(pos, mass, prm, n_mesh, acc, accumulate=True, stream=stream, pm=h)
+
+    t_total = timed(total)
+    B.ph_status(h)
+    rng = np.random.default_rng(14)
+    tg = rng.choice(ps.n, 2000, replace=False)
+    ref = opm.accel(ps.pos, ps.mass, bp.L, bp.G, bp.rs, n_mesh, targets=tg).acc
+    am = np.linalg.norm(ref, axis=1)
+    e = np.linalg.norm(acc_pm.cpu().numpy()[tg].astype(np.float64) - ref, axis=1) / np.maximum(am, 1e-3 * np.median(am))
+    B.ph_free(h)
+    return {"n_mesh": n_mesh, "pm_ms": t_pm, "split_force_step_ms": t_total,
+            "force_p99_rel_err": float(np.percentile(e, 99)), "force_max_rel_err": float(e.max()),
+            "oracle_targets": int(tg.size)}
+
+
+def _kdk_extra(B, ps, prm, n_mesh, acc_total, steps=2):
+    """Adaptive KDK block steps on the same particles (at rest at t = 0) with
+    the split force (PP + PM): force passes, time per top step and per force
+    pass.  Each event synchronises the host once (the next event tick)."""
+    import torch
+    bp = ps.boxes[0]
+    pos = np.ascontiguousarray(ps.pos.astype(np.float64))
+    mom = np.zeros_like(pos)
+    # top step chosen so that the median acceleration asks for level 1
+    # ((dt/2)^2 |a| = thr / 2 with thr = 2 eta eps); particles pulled 4 or 16
+    # times harder go to levels 2 and 3
+    eta = 0.02
+    a_med = float(torch.linalg.vector_norm(acc_total.double(), dim=1).median())
+    dt = math.sqrt(2.0 * (2.0 * eta * bp.eps) / a_med)
+    kp = B.make_kdk_params(dt=dt, eta=eta, max_level=3, n_mesh=n_mesh)
+    sim = B.ph_sim_create(pos, mom, torch.from_numpy(ps.mass).cuda(), prm, kp, 0.0)
+    _, _, _, _, _, fp0 = B.ph_sim_get(sim, ps.n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.ph_sim_step(sim, steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _, _, _, lv, _, fp = B.ph_sim_get(sim, ps.n)
+    B.ph_free(sim)
+    passes = fp - fp0
+    return {"top_steps": steps, "dt": kp.dt, "eta": eta, "force_passes": passes,
+            "ms_per_top_step": 1e3 * wall / steps, "ms_per_force_pass": 1e3 * wall / max(passes, 1),
+            "max_level": 3, "n_mesh": n_mesh, "level_counts": np.bincount(lv, minlength=4).tolist()}
 
 
 def _batched_extra(B, args, dev, stream):
@@ -558,6 +634,9 @@ def run_ours(args, rank, world, local_rank):
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
         line["table"] = _table_extra(B, ps, lv, pr, stream, t_pp, flush)
         line["tree"] = _tree_extra(B, stream, flush)
+        n_mesh = int(round(bp.L / (bp.rs / 1.25)))       # R_s = 1.25 mesh cells
+        line["pm"] = _pm_extra(B, ps, pos, mass, prm, graph, acc, stream, flush, n_mesh)
+        line["kdk"] = _kdk_extra(B, ps, prm, n_mesh, acc)
         line["batched"] = _batched_extra(B, args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, nt, dt, cores = _oracle_rate(ps, args.cpu_seconds)
