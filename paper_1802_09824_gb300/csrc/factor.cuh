@@ -45,12 +45,6 @@ __device__ __forceinline__ float exact_factor(float r2, float t, const float *po
     return ex2_sfu(r2 * c_e) * h;
 }
 
-// silu(a) = a / (1 + e^-a) with SFU ex2 and rcp (relative error ~1e-7).
-__device__ __forceinline__ float silu_sfu(float a)
-{
-    return a * rcp_sfu(1.f + ex2_sfu(a * -1.4426950408889634f));
-}
-
 // Network parameters in the flat order W1[16], b1[16], W2[16][16] (row k =
 // weights into unit k), b2[16], W3[16], b3.
 constexpr int kMlpParams = 321;
@@ -77,10 +71,31 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// The SiLU of the network in scaled units.  With z = -log2(e) a the SiLU is
+// silu(a) = -ln2 * z / (1 + 2^z): the factor -log2(e) is folded into the
+// weights and biases that produce z and -ln2 into the weights that consume
+// the activation (see mlp_lane_load), so a unit costs an SFU ex2, an add, an
+// SFU reciprocal and a multiply.  (A Newton reciprocal on the FMA pipe for
+// part of the units, to unload the SFU, measured slower.)
+__device__ __forceinline__ float silu_scaled(float z)
+{
+    return z * rcp_sfu(1.f + ex2_sfu(z));
+}
+
+// Round to BF16 (ties away from zero) with integer operations: the BF16 value
+// in the upper half of an FP32 word.  Keeps the conversion off the SFU pipe.
+__device__ __forceinline__ uint32_t bf16_round_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
+
+// Two BF16 values (upper halves of a and b) into one register, a in the low
+// half.
+__device__ __forceinline__ uint32_t pack_upper(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+
 // Per-lane share of the network for warp-level evaluation with
 // mma.sync.m16n8k16 (BF16 in, FP32 accumulate).  Lane = 4 g + q: the lane
 // owns rows g and g+8 of each 16-pair tile and hidden columns
 // {2q, 2q+1, 2q+8, 2q+9}; the 16x16 second layer is two n8 halves.
+// Weights are stored in the scaled units of silu_scaled: W1, b1 and b2
+// times -log2(e), W3 times -ln2 (W2 and b3 unchanged).
 struct MlpLane {
     float w1[4], b1[4];          // layer 1 for the lane's 4 columns
     uint32_t bhi[2][2], blo[2][2];   // W2^T fragments (hi / lo parts), per n-half
@@ -91,12 +106,14 @@ struct MlpLane {
 
 __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
 {
+    const float kz = -1.4426950408889634f;   // -log2(e)
+    const float ka = -0.6931471805599453f;   // -ln(2)
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     const int cols[4] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        L.w1[c] = w[cols[c]];
-        L.b1[c] = w[16 + cols[c]];
+        L.w1[c] = kz * w[cols[c]];
+        L.b1[c] = kz * w[16 + cols[c]];
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -109,12 +126,21 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
         L.bhi[h][1] = pack_bf16(hi[2], hi[3]);
         L.blo[h][0] = pack_bf16(lo[0], lo[1]);
         L.blo[h][1] = pack_bf16(lo[2], lo[3]);
-        L.b2[h][0] = w[288 + 8 * h + 2 * q];
-        L.b2[h][1] = w[288 + 8 * h + 2 * q + 1];
-        L.w3[h][0] = w[304 + 8 * h + 2 * q];
-        L.w3[h][1] = w[304 + 8 * h + 2 * q + 1];
+        L.b2[h][0] = kz * w[288 + 8 * h + 2 * q];
+        L.b2[h][1] = kz * w[288 + 8 * h + 2 * q + 1];
+        L.w3[h][0] = ka * w[304 + 8 * h + 2 * q];
+        L.w3[h][1] = ka * w[304 + 8 * h + 2 * q + 1];
     }
     L.b3 = w[320];
+}
+
+// Split two activations into BF16 hi and lo parts packed for the A fragment.
+__device__ __forceinline__ void split_pack(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const uint32_t h0 = bf16_round_bits(x0), h1 = bf16_round_bits(x1);
+    const float l0 = x0 - __uint_as_float(h0), l1 = x1 - __uint_as_float(h1);
+    hi = pack_upper(h0, h1);
+    lo = pack_upper(bf16_round_bits(l0), bf16_round_bits(l1));
 }
 
 // The network's factor for the warp's 32 pairs: lane i passes the input
@@ -124,7 +150,8 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
 // hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16 bits.
 __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2;
     float out = 0.f;
 #pragma unroll
     for (int tile = 0; tile < 2; tile++) {
@@ -133,20 +160,14 @@ __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
         float ha[4], hb[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            ha[c] = silu_sfu(fmaf(L.w1[c], za, L.b1[c]));
-            hb[c] = silu_sfu(fmaf(L.w1[c], zb, L.b1[c]));
+            ha[c] = silu_scaled(fmaf(L.w1[c], za, L.b1[c]));
+            hb[c] = silu_scaled(fmaf(L.w1[c], zb, L.b1[c]));
         }
-        float ah[4][2], al[4][2];   // [reg][element]
-        split_bf16(ha[0], ah[0][0], al[0][0]); split_bf16(ha[1], ah[0][1], al[0][1]);   // row g, cols 2q..
-        split_bf16(hb[0], ah[1][0], al[1][0]); split_bf16(hb[1], ah[1][1], al[1][1]);   // row g+8
-        split_bf16(ha[2], ah[2][0], al[2][0]); split_bf16(ha[3], ah[2][1], al[2][1]);   // row g, cols 2q+8..
-        split_bf16(hb[2], ah[3][0], al[3][0]); split_bf16(hb[3], ah[3][1], al[3][1]);   // row g+8
         uint32_t Ahi[4], Alo[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            Ahi[r] = pack_bf16(ah[r][0], ah[r][1]);
-            Alo[r] = pack_bf16(al[r][0], al[r][1]);
-        }
+        split_pack(ha[0], ha[1], Ahi[0], Alo[0]);   // row g, cols 2q, 2q+1
+        split_pack(hb[0], hb[1], Ahi[1], Alo[1]);   // row g+8
+        split_pack(ha[2], ha[3], Ahi[2], Alo[2]);   // row g, cols 2q+8, 2q+9
+        split_pack(hb[2], hb[3], Ahi[3], Alo[3]);   // row g+8
         float ya = 0.f, yb = 0.f;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -154,10 +175,10 @@ __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
             mma_bf16(d, Alo, L.bhi[h][0], L.bhi[h][1]);
             mma_bf16(d, Ahi, L.blo[h][0], L.blo[h][1]);
             mma_bf16(d, Ahi, L.bhi[h][0], L.bhi[h][1]);
-            ya = fmaf(L.w3[h][0], silu_sfu(d[0]), ya);
-            ya = fmaf(L.w3[h][1], silu_sfu(d[1]), ya);
-            yb = fmaf(L.w3[h][0], silu_sfu(d[2]), yb);
-            yb = fmaf(L.w3[h][1], silu_sfu(d[3]), yb);
+            ya = fmaf(L.w3[h][0], silu_scaled(d[0]), ya);
+            ya = fmaf(L.w3[h][1], silu_scaled(d[1]), ya);
+            yb = fmaf(L.w3[h][0], silu_scaled(d[2]), yb);
+            yb = fmaf(L.w3[h][1], silu_scaled(d[3]), yb);
         }
         ya += __shfl_xor_sync(0xffffffffu, ya, 1);
         ya += __shfl_xor_sync(0xffffffffu, ya, 2);
