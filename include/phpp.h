@@ -372,6 +372,38 @@ int ph_sim_step(ph_sim *sim, int32_t n_steps, void *stream);
 int ph_sim_get(const ph_sim *sim, double *pos, double *mom, float *acc, int32_t *level, double *t,
                int64_t *force_passes);
 
+/* ------------------------------------------------------------ domains
+ * Domain decomposition for several GPUs (Sec. 4.1).  A box is cut along the
+ * space-filling curve of its ground cells (the N_side^3 cells of side >=
+ * rcut the tree build starts from, N_side = 2^g from L and rcut) into runs of
+ * consecutive cells, one run per domain, balanced by work: a cell's work is
+ * its particle count times the particle count of its 27-cell neighbourhood.
+ * A domain's ghost cells are the cells of the periodic 26-neighbourhood of
+ * its own cells that it does not own; own + ghost cells hold every particle
+ * within rcut of a particle it owns, so each domain (one GPU) computes its
+ * own particles' short-range forces from its local set alone, with one
+ * exchange of particles per step and no reduction.  These three calls run on
+ * the host (no GPU, no stream); the exchange itself is the caller's (the
+ * Python package does it with torch.distributed).
+ */
+
+/* Ground grid size (*nside) and each particle's ground cell
+ * (i N_side + j) N_side + k, decided as the tree build decides it.  pos host
+ * memory [n*3] (PH_F32 or PH_F64); params: L and rcut; cell [n] host. */
+int ph_domain_cells(const void *pos, int pos_type, int64_t n, const ph_params *params, int32_t *nside,
+                    int32_t *cell);
+
+/* owner[cell] in [0, n_domains): runs of consecutive cells along the
+ * key_kind curve (PH_KEY_MORTON or PH_KEY_HILBERT) of about equal work, from
+ * the particle count of every cell (host int64 [N_side^3], summed over all
+ * ranks).  domain_cost [n_domains] (nullable): the work each domain got. */
+int ph_domain_partition(const int64_t *cell_count, int32_t nside, int32_t key_kind, int32_t n_domains,
+                        int32_t *owner, double *domain_cost);
+
+/* need[cell] for one domain (host uint8 [N_side^3]): 1 own cell, 2 ghost
+ * cell (periodic 26-neighbour of an own cell), 0 not needed. */
+int ph_domain_halo(const int32_t *owner, int32_t nside, int32_t domain, uint8_t *need);
+
 /* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph, ph_pm, ph_sim).  NULL is a no-op. */
 void ph_free(void *handle);
 

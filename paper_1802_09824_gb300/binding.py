@@ -133,6 +133,10 @@ _SIGS = {
     "ph_sim_step": ([_VP, ctypes.c_int32, _VP], ctypes.c_int),
     "ph_sim_get": ([_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                    ctypes.c_int),
+    "ph_domain_cells": ([_VP, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.POINTER(ctypes.c_int32),
+                         _VP], ctypes.c_int),
+    "ph_domain_partition": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "ph_domain_halo": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
     "ph_autotune": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(ph_params),
                      ctypes.c_int32, _VP, ctypes.POINTER(ph_tune_result)], ctypes.c_int),
 }
@@ -444,6 +448,34 @@ def ph_sim_get(sim, n):
     fp = ctypes.c_int64(0)
     _check(lib().ph_sim_get(sim.ptr, _ptr(x), _ptr(p), _ptr(a), _ptr(lv), ctypes.byref(t), ctypes.byref(fp)))
     return x, p, a, lv, t.value, fp.value
+
+
+def ph_domain_cells(pos, params):
+    """(N_side, ground cell of every particle) for host positions [N,3]
+    (numpy or CPU tensor, float32 or float64); runs on the host."""
+    a = np.ascontiguousarray(pos.numpy() if hasattr(pos, "numpy") else pos)
+    cells = np.zeros(a.shape[0], np.int32)
+    ns = ctypes.c_int32(0)
+    _check(lib().ph_domain_cells(_ptr(a), _pos_type(a), int(a.shape[0]), ctypes.byref(params), ctypes.byref(ns),
+                                 _ptr(cells)))
+    return ns.value, cells
+
+
+def ph_domain_partition(cell_count, nside, key_kind, n_domains):
+    """(owner int32 [N_side^3], work per domain float64 [n_domains])."""
+    c = np.ascontiguousarray(np.asarray(cell_count, np.int64))
+    owner = np.zeros(c.size, np.int32)
+    cost = np.zeros(int(n_domains), np.float64)
+    _check(lib().ph_domain_partition(_ptr(c), int(nside), int(key_kind), int(n_domains), _ptr(owner), _ptr(cost)))
+    return owner, cost
+
+
+def ph_domain_halo(owner, nside, domain):
+    """need uint8 [N_side^3]: 1 own cell, 2 ghost cell, 0 not needed."""
+    o = np.ascontiguousarray(np.asarray(owner, np.int32))
+    need = np.zeros(o.size, np.uint8)
+    _check(lib().ph_domain_halo(_ptr(o), int(nside), int(domain), _ptr(need)))
+    return need
 
 
 def ph_launch_counter():

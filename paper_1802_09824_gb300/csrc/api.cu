@@ -128,7 +128,10 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static int ground_level(double L, double rcut)
+// Ground level g of a box: the finest N_side = 2^g (g <= kGroundMax) whose
+// cells are at least rcut wide (Sec. 4.3: a cell and its 26 neighbours hold
+// every particle within rcut of the cell).
+int ground_level(double L, double rcut)
 {
     int g = 0;
     while (g < kGroundMax && L / (double)(1 << (g + 1)) >= rcut) g++;

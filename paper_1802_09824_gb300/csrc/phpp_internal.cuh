@@ -61,6 +61,9 @@ inline float float_at_or_above(double L)
     return f;
 }
 
+// Ground level of a box (N_side = 2^g cells of side >= rcut); api.cu.
+int ground_level(double L, double rcut);
+
 // Streaming multiprocessors of the current device (persistent grids).
 inline int sm_count()
 {
