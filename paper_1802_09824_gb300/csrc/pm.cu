@@ -1,7 +1,8 @@
 // Long-range side of the force split: the particle-mesh (PM) part of
 // Sec. 3.1 on one periodic box.
 //
-//   1. CIC assignment of the masses to an N^3 mesh (k_pm_deposit): 64-bit
+//   1. CIC assignment of the masses to an N^3 mesh (k_pm_deposit): the cell
+//      and fraction in FP64, the CIC weights in FP32, summed as 64-bit
 //      fixed-point atomics, so the node masses do not depend on the order of
 //      the additions (replays are bit-identical).
 //   2. FFT of the node masses (cuFFT, real to complex, FP32).
@@ -138,21 +139,24 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
         const int ix = pm_cell(x, L, inv_dg, N, fx);
         const int iy = pm_cell(y, L, inv_dg, N, fy);
         const int iz = pm_cell(z, L, inv_dg, N, fz);
-        const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+        // weights and products in FP32 (this GPU's FP64 pipe is narrow): a
+        // node's share carries ~3 FP32 roundings, the integer sums none
+        const float gx = (float)fx, gy = (float)fy, gz = (float)fz;
+        const float wx[2] = {1.f - gx, gx}, wy[2] = {1.f - gy, gy};
+        const float mS = (float)(m * S);
+        const float wzm[2] = {(1.f - gz) * mS, gz * mS};
         const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
         const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
         const int jz[2] = {iz, iz + 1 == N ? 0 : iz + 1};
-        const double mS = m * S;
-        const double wzm[2] = {wz[0] * mS, wz[1] * mS};
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
             for (int b = 0; b < 2; b++) {
-                const double wab = wx[a] * wy[b];
+                const float wab = wx[a] * wy[b];
                 const int64_t row = ((int64_t)jx[a] * N + jy[b]) * N;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const long long q = __double2ll_rn(wab * wzm[c]);
+                    const long long q = __float2ll_rn(wab * wzm[c]);
                     if (q) atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
                 }
             }
@@ -163,9 +167,9 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
 __global__ void k_pm_unfix(const unsigned long long *mesh_q, int64_t cells, int64_t n, const uint32_t *mmax_bits,
                            float *mesh_r)
 {
-    const double inv = 1.0 / pm_scale(mmax_bits, n);
+    const float inv = (float)(1.0 / pm_scale(mmax_bits, n));   // a power of two
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
-        mesh_r[i] = (float)((double)(long long)mesh_q[i] * inv);
+        mesh_r[i] = __ll2float_rn((long long)mesh_q[i]) * inv;
 }
 
 // Multiply the half spectrum by the filtered Green's function.  c0 folds
@@ -225,8 +229,8 @@ __global__ void k_pm_interp(const void *pos, int64_t n, double L, double inv_dg,
         const int ix = pm_cell(x, L, inv_dg, N, fx);
         const int iy = pm_cell(y, L, inv_dg, N, fy);
         const int iz = pm_cell(z, L, inv_dg, N, fz);
-        const float wx[2] = {(float)(1.0 - fx), (float)fx}, wy[2] = {(float)(1.0 - fy), (float)fy},
-                    wz[2] = {(float)(1.0 - fz), (float)fz};
+        const float gx = (float)fx, gy = (float)fy, gz = (float)fz;
+        const float wx[2] = {1.f - gx, gx}, wy[2] = {1.f - gy, gy}, wz[2] = {1.f - gz, gz};
         const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
         const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
         const int jz[2] = {iz, iz + 1 == N ? 0 : iz + 1};

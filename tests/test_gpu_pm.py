@@ -1,8 +1,9 @@
 """Long-range PM side through the C ABI against the FP64 oracle (oracle/pm.py).
 
-Tolerances.  The node masses are 64-bit fixed-point sums of FP64 products
-(resolution 2^-62 of n max|m|), so they match the oracle's FP64 sums to
-~1e-13 of the largest node.  Everything after is FP32: the FFT (relative
+Tolerances.  The node masses are 64-bit fixed-point sums (resolution 2^-62
+of n max|m|) of CIC shares computed in FP32 from the FP64 fraction: three
+FP32 roundings per share (~2^-23 relative), so they match the oracle's FP64
+sums to ~1e-7 of a node (gate 1e-6).  Everything after is FP32: the FFT (relative
 error ~ eps32 log2(N^3) of the field's norm), the Green's function tables
 and the central difference; a numpy emulation of the same FP32 steps gives
 per-particle errors e_i (guarded by tau = 1e-3 median |a|) of p99 2-5e-6 and
@@ -49,7 +50,8 @@ def _gpu_pm(B, ps, n_mesh, pos_dtype=np.float32, host=False, mass=True, pot=Fals
 
 
 @pytest.mark.parametrize("name,scale,n_mesh", [("uniform_small", None, 32), ("zeldovich_128", 32, 32),
-                                               ("nfw_mix_256", 32, 32), ("zeldovich_128", 48, 64)])
+                                               ("nfw_mix_256", 32, 32), ("zeldovich_128", 48, 64),
+                                               ("uniform_small", None, 24)])
 def test_pm_matches_oracle(gpu_lib, name, scale, n_mesh):
     ps = synth.workload(name, scale=scale)
     bp = ps.boxes[0]
@@ -63,7 +65,8 @@ def test_pm_matches_oracle(gpu_lib, name, scale, n_mesh):
 
 
 def test_pm_steps_match_oracle(gpu_lib):
-    # step 1 (node masses) to ~1e-13, steps 2-5 on the mesh to FP32 accuracy
+    # step 1 (node masses) to FP32 accuracy of the shares, steps 2-5 on the
+    # mesh to FP32 accuracy
     ps = synth.workload("nfw_mix_256", scale=32)
     bp = ps.boxes[0]
     n = 32
@@ -71,8 +74,8 @@ def test_pm_steps_match_oracle(gpu_lib):
     v = gpu_lib.ph_pm_get_view(h)
     grid = v["mass_fixed"].cpu().numpy().astype(np.float64) * v["mass_unit"]
     ref_grid = pm.cic_assign(ps.pos, ps.mass, bp.L, n)
-    assert np.max(np.abs(grid - ref_grid)) <= 1e-12 * np.max(ref_grid)
-    assert abs(grid.sum() - ps.mass.astype(np.float64).sum()) <= 1e-12 * ps.mass.sum()
+    assert np.max(np.abs(grid - ref_grid)) <= 1e-6 * np.max(ref_grid)
+    assert abs(grid.sum() - ps.mass.astype(np.float64).sum()) <= 1e-6 * ps.mass.sum()
     mesh = v["mesh"].cpu().numpy().astype(np.float64)
     phi = pm.potential(ref_grid, bp.L, bp.G, bp.rs)
     macc = pm.mesh_accel(phi, bp.L)
