@@ -227,6 +227,18 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
 /* Replay a captured step on `stream` (asynchronous). */
 int ph_graph_launch(ph_graph *graph, void *stream);
 
+/*
+ * Replay with host buffers: copy h_pos [n*3] (the pos_type of the capture)
+ * and, when not NULL, h_mass [n] into the device buffers the graph reads,
+ * replay it, and copy the accelerations into h_acc [n*3] (caller order).
+ * Returns after the copies have completed (synchronises the stream once) and
+ * reports the step's latched status: PH_ERR_CAPACITY means the pair list
+ * outgrew its capacity (rebuild the pairs and the graph), PH_ERR_NONFINITE a
+ * non-finite input.  h_mass must be NULL for a graph captured without
+ * masses.  Pinned host memory makes the copies asynchronous DMA.
+ */
+int ph_graph_launch_host(ph_graph *graph, const void *h_pos, const float *h_mass, float *h_acc, void *stream);
+
 /* Kernels launched by one replay. */
 int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
 

@@ -124,6 +124,7 @@ _SIGS = {
     "ph_graph_create": ([_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP,
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
+    "ph_graph_launch_host": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "ph_graph_kernels": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ph_pm_accel": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.c_int32, _VP, _VP,
                      ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -375,6 +376,11 @@ def ph_graph_create(leaves, pairs, pos, mass, g_mode, mlp, acc, headroom=0.25, s
 
 def ph_graph_launch(graph, stream=None):
     return _check(lib().ph_graph_launch(graph.ptr, _stream(stream)))
+
+
+def ph_graph_launch_host(graph, pos, mass, acc, stream=None):
+    """Copy host pos/mass in, replay, copy acc out (synchronises)."""
+    return _check(lib().ph_graph_launch_host(graph.ptr, _ptr(pos), _ptr(mass), _ptr(acc), _stream(stream)))
 
 
 def ph_graph_kernels(graph):

@@ -28,6 +28,14 @@ struct ph_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;        // our kernel launches per replay
+    // the buffers the capture reads and writes (for host-buffer replays)
+    const void *d_pos = nullptr;
+    const float *d_mass = nullptr;
+    float *d_acc = nullptr;
+    int pos_type = PH_F32;
+    int64_t n = 0;
+    ph_leaves *leaves = nullptr;
+    ph_pairs *pairs = nullptr;
 };
 
 using namespace phpp;
@@ -109,6 +117,13 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     }
     // the capture only recorded the launches; do not count them as run
     count_launch((int)-g->kernels);
+    g->d_pos = d_pos;
+    g->d_mass = d_mass;
+    g->d_acc = d_acc;
+    g->pos_type = pos_type;
+    g->n = leaves->n;
+    g->leaves = leaves;
+    g->pairs = pairs;
     leaves->last_stream = caller;
     if (pairs) pairs->last_stream = caller;
     *out = g;
@@ -124,6 +139,34 @@ int ph_graph_launch(ph_graph *g, void *stream)
     int rc = cuda_check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "graph launch");
     if (!rc) count_launch((int)g->kernels);
     return rc;
+}
+
+int ph_graph_launch_host(ph_graph *g, const void *h_pos, const float *h_mass, float *h_acc, void *stream)
+{
+    if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
+    if (g->n > 0 && (!h_pos || !h_acc)) return fail(PH_ERR_ARG, "h_pos and h_acc must not be NULL");
+    if (h_mass && !g->d_mass) return fail(PH_ERR_ARG, "the graph was captured without masses");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)g->n;
+    const size_t pbytes = n * 3 * (g->pos_type == PH_F64 ? 8 : 4);
+    int rc = PH_OK;
+    if (n) rc = cuda_check(cudaMemcpyAsync(const_cast<void *>(g->d_pos), h_pos, pbytes, cudaMemcpyDefault, s),
+                           "copy positions");
+    if (!rc && n && h_mass)
+        rc = cuda_check(cudaMemcpyAsync(const_cast<float *>(g->d_mass), h_mass, n * 4, cudaMemcpyDefault, s),
+                        "copy masses");
+    if (!rc) rc = ph_graph_launch(g, stream);
+    if (!rc && n) rc = cuda_check(cudaMemcpyAsync(h_acc, g->d_acc, n * 12, cudaMemcpyDefault, s), "copy acc");
+    uint32_t st[2] = {0, 0};
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(&st[0], g->leaves->status.p, 4, cudaMemcpyDeviceToHost, s), "status");
+    if (!rc && g->pairs)
+        rc = cuda_check(cudaMemcpyAsync(&st[1], g->pairs->status.p, 4, cudaMemcpyDeviceToHost, s), "status");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "host replay sync");
+    if (rc) return rc;
+    const uint32_t any = st[0] | st[1];
+    if (any & ST_NONFINITE) return fail(PH_ERR_NONFINITE, "non-finite position or mass");
+    if (any & ST_CAPACITY) return fail(PH_ERR_CAPACITY, "pair list capacity exceeded: rebuild the pairs and the graph");
+    return PH_OK;
 }
 
 int ph_graph_kernels(const ph_graph *g, int64_t *kernels)

@@ -85,6 +85,39 @@ def test_graph_capacity_overflow_is_latched(gpu_lib):
         B.ph_free(h)
 
 
+def test_graph_replay_with_host_buffers(gpu_lib):
+    # ph_graph_launch_host: host positions and masses copied in, the step
+    # replayed, accelerations copied out -- the same bits as a device replay,
+    # from pinned and from pageable host memory; an overflow is reported
+    import torch
+    B = gpu_lib
+    ps = synth.workload("uniform_small", scale=5000)
+    pos, mass, acc = _tensors(ps)
+    prm = _params(B, ps)
+    lv = B.ph_build_leaves(pos, mass, prm[0])
+    pr = B.ph_leaf_pairs(lv)
+    g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.1)
+    B.ph_graph_launch(g)
+    torch.cuda.synchronize()
+    ref = acc.cpu().numpy().copy()
+    pos.zero_()                                  # the host replay must bring the positions back
+    for pinned in (True, False):
+        hp = torch.from_numpy(ps.pos.copy())
+        hm = torch.from_numpy(ps.mass.copy())
+        ha = torch.full((ps.n, 3), float("nan"))
+        if pinned:
+            hp, hm, ha = hp.pin_memory(), hm.pin_memory(), ha.pin_memory()
+        B.ph_graph_launch_host(g, hp, hm, ha)
+        np.testing.assert_array_equal(ha.numpy(), ref)
+    check_parity(ref, oracle_accel(ps))
+    squeezed = torch.from_numpy((ps.pos * 0.15).astype(np.float32))
+    with pytest.raises(B.PhError) as ei:
+        B.ph_graph_launch_host(g, squeezed, None, torch.zeros((ps.n, 3)))
+    assert ei.value.code == B.PH_ERR_CAPACITY
+    for h in (g, pr, lv):
+        B.ph_free(h)
+
+
 @pytest.mark.parametrize("gs", [8, 16, 32])
 def test_group_sizes_match_the_oracle(gpu_lib, gs):
     ps = synth.workload("zeldovich_128", scale=32)
