@@ -19,7 +19,7 @@
 #include <new>
 #include <vector>
 
-#include "phpp_internal.cuh"
+#include "handles.cuh"
 
 struct ph_sim {
     uint32_t kind = phpp::KIND_SIM;
@@ -34,6 +34,8 @@ struct ph_sim {
     ph_leaves *lv = nullptr;
     ph_pairs *pr = nullptr;
     ph_pm *pm = nullptr;
+    ph_graph *graph = nullptr;    // build + pairs + PP captured once (fixed pair capacity)
+    int64_t rebuilds = 0;         // pair lists regrown after a capacity overflow
 };
 
 namespace phpp {
@@ -72,9 +74,13 @@ __device__ __forceinline__ int level_of(float ax, float ay, float az, double dt,
     return k;
 }
 
+// guard: the pair list's status word; when the force pass overflowed the
+// list (its accelerations are incomplete) the kick does nothing, so the host
+// can rebuild the list, redo the force pass and launch the kick again.
 __global__ void k_sim_kick(int64_t n, const float *acc, double *p, int32_t *level, int32_t *start, int32_t *next,
-                           KickArgs ka)
+                           const uint32_t *guard, KickArgs ka)
 {
+    if (guard && (*guard & ST_CAPACITY)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float ax = acc[3 * i], ay = acc[3 * i + 1], az = acc[3 * i + 2];
         const double a[3] = {ax, ay, az};
@@ -181,6 +187,8 @@ double step_scale(const ph_kdk_params &k, double t) { return k.clock == PH_CLOCK
 
 void sim_release(ph_sim *h)
 {
+    if (h->graph) ph_free(h->graph);
+    h->graph = nullptr;
     if (h->pm) ph_free(h->pm);
     if (h->pr) ph_free(h->pr);
     if (h->lv) ph_free(h->lv);
@@ -191,36 +199,86 @@ void sim_release(ph_sim *h)
     for (DevBuf *b : bufs) release(*b);
 }
 
-// One force pass at the current positions: PP (short range) then PM (long
-// range, added).
-int force_pass(ph_sim *h, cudaStream_t s)
+// The long-range part added onto the short-range accelerations.
+int add_pm(ph_sim *h, cudaStream_t s)
+{
+    if (h->kp.n_mesh <= 0) return PH_OK;
+    const float *m = h->has_mass ? static_cast<const float *>(h->mass.p) : nullptr;
+    const int rc = ph_pm_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.n_mesh, static_cast<float *>(h->acc.p),
+                               nullptr, 1, s, &h->pm);
+    return rc < 0 ? rc : PH_OK;
+}
+
+// A full force pass with sizing (host synchronisations): build, a pair list
+// sized for the current positions, PP, PM; then the build, pairs and PP are
+// captured as one graph with a fixed pair capacity (25 % headroom) for the
+// following passes.
+int force_pass_sized(ph_sim *h, cudaStream_t s)
 {
     const float *m = h->has_mass ? static_cast<const float *>(h->mass.p) : nullptr;
     float *acc = static_cast<float *>(h->acc.p);
-    int rc = ph_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.g_mode, nullptr, acc, s, &h->lv, &h->pr);
-    if (rc < 0) return rc;
-    if (h->kp.n_mesh > 0) {
-        rc = ph_pm_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.n_mesh, acc, nullptr, 1, s, &h->pm);
-        if (rc < 0) return rc;
+    if (h->graph) {
+        ph_free(h->graph);
+        h->graph = nullptr;
     }
-    h->force_passes++;
-    return PH_OK;
+    int rc = PH_OK;
+    if (h->pr) {
+        h->pr->fixed_capacity = false;           // let the list be sized again
+        rc = cuda_check(cudaMemsetAsync(h->pr->status.p, 0, 4, s), "clear the overflow");
+        if (rc) return rc;
+    }
+    rc = ph_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.g_mode, nullptr, acc, s, &h->lv, &h->pr);
+    if (rc < 0) return rc;
+    rc = add_pm(h, s);
+    if (rc) return rc;
+    rc = ph_graph_create(h->lv, h->pr, h->x.p, PH_F64, m, h->kp.g_mode, nullptr, acc, 0.25, s, &h->graph);
+    return rc < 0 ? rc : PH_OK;
 }
 
+// One force pass at the current positions: the captured build + pairs + PP
+// (no host synchronisation) then PM added.  A pair list that outgrew its
+// capacity is latched in its status word, which the kick checks.
+int force_pass(ph_sim *h, cudaStream_t s)
+{
+    int rc;
+    if (h->graph) {
+        rc = ph_graph_launch(h->graph, s);
+        if (!rc) rc = add_pm(h, s);
+    } else {
+        rc = force_pass_sized(h, s);
+    }
+    if (!rc) h->force_passes++;
+    return rc;
+}
+
+// The kicks of one event, guarded by the pair list's status; reads back the
+// next event tick and the status with one synchronisation.  After an
+// overflow (the guarded kick did nothing) the force pass is redone with a
+// list sized afresh and the kick launched again.
 int launch_kick(ph_sim *h, const KickArgs &ka, cudaStream_t s, int32_t *next_host)
 {
     int32_t *nx = static_cast<int32_t *>(h->next.p);
-    int rc = cuda_check(cudaMemsetAsync(nx, 0x7f, 4, s), "reset event");
-    if (rc) return rc;
-    k_sim_kick<<<grid_of(h->n), kSimThreads, 0, s>>>(h->n, static_cast<const float *>(h->acc.p),
-                                                    static_cast<double *>(h->p.p), static_cast<int32_t *>(h->level.p),
-                                                    static_cast<int32_t *>(h->start.p), nx, ka);
-    count_launch();
-    rc = cuda_check(cudaGetLastError(), "kick kernel");
-    if (rc || ka.last) return rc;
-    rc = cuda_check(cudaMemcpyAsync(next_host, nx, 4, cudaMemcpyDeviceToHost, s), "read event");
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "event sync");
-    return rc;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        const uint32_t *guard = h->pr ? static_cast<const uint32_t *>(h->pr->status.p) : nullptr;
+        int rc = cuda_check(cudaMemsetAsync(nx, 0x7f, 4, s), "reset event");
+        if (rc) return rc;
+        k_sim_kick<<<grid_of(h->n), kSimThreads, 0, s>>>(h->n, static_cast<const float *>(h->acc.p),
+                                                        static_cast<double *>(h->p.p),
+                                                        static_cast<int32_t *>(h->level.p),
+                                                        static_cast<int32_t *>(h->start.p), nx, guard, ka);
+        count_launch();
+        rc = cuda_check(cudaGetLastError(), "kick kernel");
+        uint32_t st = 0;
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(next_host, nx, 4, cudaMemcpyDeviceToHost, s), "read event");
+        if (!rc && guard) rc = cuda_check(cudaMemcpyAsync(&st, guard, 4, cudaMemcpyDeviceToHost, s), "read status");
+        if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "event sync");
+        if (rc) return rc;
+        if (!(st & ST_CAPACITY)) return PH_OK;
+        h->rebuilds++;
+        rc = force_pass_sized(h, s);     // the kick above did nothing: redo the pass, then kick
+        if (rc) return rc;
+    }
+    return fail(PH_ERR_CAPACITY, "pair list overflow persisted after resizing");
 }
 
 int top_step(ph_sim *h, cudaStream_t s)
@@ -331,7 +389,8 @@ int ph_sim_create(const double *pos, const double *mom, const float *mass, int64
         rc = cuda_check(cudaGetLastError(), "wrap kernel");
     }
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "create sync");
-    if (!rc) rc = force_pass(h, s);
+    if (!rc) rc = force_pass_sized(h, s);
+    if (!rc) h->force_passes++;
     if (rc) {
         sim_free(h);
         return rc;
