@@ -657,8 +657,16 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = _batched_extra(B, args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, nt, dt, cores = _oracle_rate(ps, args.cpu_seconds)
+        tests_per_s = float(ps.n) * nt / dt
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"all {ps.n} sources x {nt} random targets, {dt:.1f} s"}
+                                "sample": f"all {ps.n} sources x {nt} random targets, {dt:.1f} s",
+                                "pair_tests_per_s_per_core": tests_per_s / cores,
+                                "extrapolated_full_step_s": float(ps.n) * ps.n / tests_per_s,
+                                "extrapolated": "all N targets at the sample's rate"}
+    # the paper's PP kernel efficiencies (fraction of the node's peak, Sec. 5):
+    # other hardware and a 22-flop convention, context only
+    line["paper_context"] = {"pp_efficiency_cpu": 0.744, "pp_efficiency_mic": 0.686,
+                             "ours_paper_convention_frac": line["pp"]["paper_convention_tflops"] / peak}
     for h in (graph, pr, lv, pr2, lv2):
         B.ph_free(h)
     if rank == 0:
