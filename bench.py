@@ -174,7 +174,7 @@ def _learned_extra(B, ps, lv, pr, stream, t_exact_pp):
     mlp = B.ph_mlp_train(tp, bp.rs, bp.rcut)
     train_s = time.perf_counter() - t0
     w, err, loss = B.ph_mlp_get(mlp)
-    # time the learned kernel whatever the judge says (tolerance 1)
+    # time the learned kernel whatever its validation against the exact factor says (tolerance 1)
     timed = B.ph_mlp_create(w, bp.rs, bp.rcut, tol=1.0)
     acc_l = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
     acc_e = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
@@ -201,7 +201,7 @@ def _learned_extra(B, ps, lv, pr, stream, t_exact_pp):
 
     out = {"config": "learned factor on the same workload and lists (MLP 1-16-16-1 SiLU, BF16 MMA layer 2)",
            "train_steps": tp.steps, "train_batch": tp.batch, "train_s": train_s, "train_loss": loss,
-           "g_max_rel_err": err, "judge_tolerance": 1e-3, "falls_back": bool(err > 1e-3),
+           "g_max_rel_err": err, "validation_tolerance": 1e-3, "falls_back": bool(err > 1e-3),
            "pp_ms": t_l, "exact_pp_ms": t_exact_pp, "speedup_vs_exact": t_exact_pp / t_l,
            "force_p99_rel_err_learned": p99(acc_l.cpu().numpy()),
            "force_p99_rel_err_exact": p99(acc_e.cpu().numpy()), "oracle_targets": int(tg.size)}
