@@ -177,3 +177,32 @@ def test_kdk_recovers_when_the_pair_list_outgrows_its_capacity(gpu_lib):
     d -= L * np.round(d / L)
     assert np.max(np.abs(d)) <= 1e-6
     B.ph_free(sim)
+
+
+def test_three_body_split_orbit_matches_oracle(gpu_lib):
+    # the paper's three-body test of KDK under the force split (see
+    # tests/test_oracle_kdk.py::three_body), 16 top steps (257 force passes)
+    # through ph_sim against the FP64 oracle integrator
+    from test_oracle_kdk import three_body
+    B = gpu_lib
+    ref, hist = three_body(0.1, 0.05, 4, 16)
+    L, nm = 4.0, 32
+    rs = 1.25 * L / nm
+    M, m, R, s = 1.0, 0.01, 1.0, 0.05
+    c = np.array([2.0, 2.0, 2.0])
+    vorb, vb = math.sqrt(M / R), math.sqrt(2 * m / s) / 2
+    pos = np.array([c, c + [R, -s / 2, 0], c + [R, s / 2, 0]])
+    mom = np.array([[0, -2 * m * vorb / M, 0], [vb, vorb, 0], [-vb, vorb, 0]])
+    mass = np.array([M, m, m], np.float32)
+    prm = B.make_params(L, 1.0, 0.005, rs, 4.5 * rs, 32)
+    sim = B.ph_sim_create(pos, mom, mass, prm, B.make_kdk_params(0.1, 0.05, 4, nm), 0.0)
+    B.ph_sim_step(sim, 16)
+    x, p, a, lv, t, fp = B.ph_sim_get(sim, 3)
+    assert list(lv) == list(ref.level) and fp == ref.force_passes
+    d = x - ref.x
+    d -= L * np.round(d / L)
+    # FP32 forces (relative error ~1e-6) over 257 passes of a regular orbit:
+    # a small fraction of the coarse run's own step error (2e-3)
+    assert np.abs(d).max() < 1e-4
+    assert np.abs(p - ref.p).max() < 1e-4 * np.abs(ref.p).max()
+    B.ph_free(sim)

@@ -1,7 +1,8 @@
 """Pins of the adaptive KDK oracle (oracle/kdk.py): the step criterion
 against its closed form, the clocks against closed forms and an independent
-change of variable, second-order convergence on a Kepler orbit, time
-reversibility, and block steps against a plain fixed-step loop."""
+change of variable, second-order convergence on a Kepler orbit and on the
+paper's three-body test of the force split, time reversibility, and block
+steps against a plain fixed-step loop."""
 import math
 
 import numpy as np
@@ -158,3 +159,45 @@ def test_adaptive_levels_follow_fine_reference():
     d = np.minimum(d, 1.0 - d)
     assert d.max() < 2e-4
     assert ad.force_passes < fine.force_passes
+
+
+def three_body(dt, eta, max_level, steps):
+    """Sec. 3.5's test of KDK under the force split: a close binary (two
+    masses 0.01 at separation 0.05 < R_s, bound by the short-range force)
+    on an orbit of radius 1 > R_cut around a unit mass (the long-range PM
+    force), in a periodic box of side 4 with a 32^3 mesh.  Returns the
+    simulation and, per top step, the binary's centre relative to the
+    central mass and its separation vector (minimum image)."""
+    L, nm = 4.0, 32
+    rs = 1.25 * L / nm
+    M, m, R, s = 1.0, 0.01, 1.0, 0.05
+    c = np.array([2.0, 2.0, 2.0])
+    vorb, vb = math.sqrt(M / R), math.sqrt(2 * m / s) / 2
+    pos = np.array([c, c + [R, -s / 2, 0], c + [R, s / 2, 0]])
+    mom = np.array([[0, -2 * m * vorb / M, 0], [vb, vorb, 0], [-vb, vorb, 0]])
+    mass = np.array([M, m, m], np.float32)
+    sim = kdk.Sim(pos, mom, mass, L, 1.0, 0.005, rs, 4.5 * rs, nm, dt, eta, max_level)
+    hist = []
+    for _ in range(steps):
+        sim.top_step()
+        cm = (sim.x[1] + sim.x[2]) / 2 - sim.x[0]
+        sep = sim.x[1] - sim.x[2]
+        hist.append(np.r_[cm - L * np.round(cm / L), sep - L * np.round(sep / L)])
+    return sim, np.array(hist)
+
+
+def test_three_body_split_orbit_is_bound_and_second_order():
+    # a quarter of the outer orbit; the binary's steps are 1/16 of the top
+    # step (level 4), then 1/32 and 1/64 of it in two finer runs (eta / 4,
+    # eta / 16): the binary stays bound and the coarse run converges to the
+    # fine one at second order (differences 16 : 4 : 1 -> ratio 5)
+    a, ha = three_body(0.1, 0.05, 4, 16)
+    b, hb = three_body(0.1, 0.05 / 4, 5, 16)
+    c, hc = three_body(0.1, 0.05 / 16, 6, 16)
+    assert list(a.level) == [0, 4, 4] and list(c.level) == [2, 6, 6]
+    sep = np.linalg.norm(ha[:, 3:], axis=1)
+    assert sep.min() > 0.9 * 0.05 and sep.max() < 1.1 * 0.05
+    d_ac = np.abs(ha[-1] - hc[-1]).max()
+    d_bc = np.abs(hb[-1] - hc[-1]).max()
+    assert d_ac < 5e-3
+    assert 3.5 < d_ac / d_bc < 7.0
