@@ -74,6 +74,24 @@ def test_partition_is_contiguous_on_the_curve_and_balanced(key_kind, n_domains):
     assert np.all(np.abs(cost - w.sum() / n_domains) <= w.max() + 1e-9)
 
 
+def test_more_domains_than_cells():
+    # 8^3 = 512 cells cut for 700 domains: every cell owned once, some
+    # domains empty (their halo is empty too), work still covered
+    pos, _ = _particles()
+    ns, cells = B.ph_domain_cells(pos, _params())
+    counts = np.bincount(cells, minlength=ns ** 3)
+    owner, cost = B.ph_domain_partition(counts, ns, B.PH_KEY_HILBERT, 700)
+    used = np.unique(owner)
+    assert used.size <= ns ** 3 and owner.max() < 700
+    empty = sorted(set(range(700)) - set(used.tolist()))
+    assert empty and np.all(cost[empty] == 0)
+    assert not B.ph_domain_halo(owner, ns, empty[0]).any()
+    c3 = counts.reshape(ns, ns, ns).astype(np.float64)
+    reach = sum(np.roll(np.roll(np.roll(c3, a, 0), b, 1), c, 2)
+                for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1))
+    assert np.isclose(cost.sum(), (c3 * reach).sum())
+
+
 def test_halo_is_the_26_neighbourhood():
     pos, _ = _particles()
     ns, cells = B.ph_domain_cells(pos, _params())

@@ -182,3 +182,20 @@ def test_pm_full_size_zeldovich_128_sampled(gpu_lib):
     q, m = _check(got[t], ref)
     print(f"PM 128^3: p99 {q:.2e} max {m:.2e}")
     gpu_lib.ph_free(h)
+
+
+def test_pm_positions_outside_the_box(gpu_lib):
+    # coordinates anywhere on the real line: the FP64 wrap branch of the cell
+    # decision, the same result as the wrapped set (and as the oracle)
+    ps = synth.workload("uniform_small", scale=3000)
+    bp = ps.boxes[0]
+    rng = np.random.default_rng(17)
+    shift = rng.integers(-3, 4, size=ps.pos.shape).astype(np.float64) * bp.L
+    moved = synth.ParticleSet(ps.pos.astype(np.float64) + shift, ps.mass, ps.boxes, ps.offsets, "moved")
+    ref = pm.accel(moved.pos, moved.mass, bp.L, bp.G, bp.rs, 32).acc
+    a, _, h1 = _gpu_pm(gpu_lib, moved, 32, pos_dtype=np.float64)
+    _check(a, ref)
+    b, _, h2 = _gpu_pm(gpu_lib, ps, 32, pos_dtype=np.float64)
+    _check(b, ref)
+    for h in (h1, h2):
+        gpu_lib.ph_free(h)
