@@ -338,8 +338,9 @@ int ph_pm_get_view(const ph_pm *pm, ph_pm_view *out);
  * opening half kick; then, at each event (the earliest end of any
  * particle's current step, on a timeline of 2^max_level ticks), all
  * particles drift to it, the force is recomputed for all (ph_accel: build,
- * pairs, short-range PP; then ph_pm_accel added when n_mesh > 0), the
- * particles whose step ends take their closing half kick and, before the
+ * pairs, short-range PP; then ph_pm_accel added when n_mesh > 0) for the
+ * particles whose step ends there (only their groups get source lists),
+ * those particles take their closing half kick and, before the
  * top step's end, a new level (refined until its step length divides the
  * elapsed ticks) and an opening half kick.  The level is the smallest k in
  * [0, max_level] with (dt_phys / 2^k)^2 |a| <= 2 eta eps_step, decided in
@@ -378,9 +379,10 @@ int ph_sim_create(const double *pos, const double *mom, const float *mass, int64
 int ph_sim_step(ph_sim *sim, int32_t n_steps, void *stream);
 
 /* Current state (each output host or device, nullable): positions and
- * momenta [n*3] float64, last accelerations [n*3] float32, levels [n] of
- * the last top step, time, and force passes so far.  Synchronises and
- * reports any status latched by the force calls. */
+ * momenta [n*3] float64, accelerations [n*3] float32 of the last force pass
+ * (after a whole top step: of every particle), levels [n] of the last top
+ * step, time, and force passes so far.  Synchronises and reports any status
+ * latched by the force calls. */
 int ph_sim_get(const ph_sim *sim, double *pos, double *mom, float *acc, int32_t *level, double *t,
                int64_t *force_passes);
 

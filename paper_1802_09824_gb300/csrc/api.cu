@@ -183,7 +183,8 @@ static void free_leaves(ph_leaves *h)
                       &h->vals_alt, &h->xw, &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag,
                       &h->leaf_scan, &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4,
                       &h->leaf_h4, &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext, &h->work, &h->acc_tmp, &h->table, &h->group_cell, &h->group_box,
-                      &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp};
+                      &h->pos_leaf, &h->pos_group, &h->cell_leaf_first, &h->counts, &h->status, &h->temp,
+                      &h->group_act, &h->group_act_scan, &h->active_list};
     for (DevBuf *b : bufs) release(*b);
 }
 

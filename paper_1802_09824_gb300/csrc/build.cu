@@ -452,6 +452,29 @@ inline int grid_for(int64_t n, int threads = kThreads, int cap = 152 * 16)
     return (int)(b < cap ? b : cap);
 }
 
+// Active-particle mode: flag the groups that hold at least one particle
+// flagged active (flags in caller order, perm maps sorted -> caller row).
+__global__ void k_group_active(const int32_t *gfirst, const int32_t *n_groups, const int32_t *perm,
+                               const uint8_t *active, int32_t *gflag)
+{
+    const int ng = *n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int f = 0;
+        for (int j = gfirst[g]; j < gfirst[g + 1] && !f; j++) f = active[perm[j]] ? 1 : 0;
+        gflag[g] = f;
+    }
+}
+
+// The flagged groups in order, and their number into *n_active.
+__global__ void k_active_list(const int32_t *gflag, const int32_t *gscan, const int32_t *n_groups, int32_t *list,
+                              int32_t *n_active)
+{
+    const int ng = *n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        if (gflag[g]) list[gscan[g]] = g;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_active = gscan[ng];
+}
+
 }  // namespace
 
 // h(u) = exp(u^2) erfc(u) + 2u/sqrt(pi), so that Eq. (split) is f = exp(-u^2) h(u)
@@ -589,6 +612,18 @@ int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float
     int32_t *cnt = static_cast<int32_t *>(h->counts.p);
     cudaMemcpyAsync(cnt + 0, lscan + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(cnt + 1, gscan + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (h->active && n > 0) {
+        // the groups to sum in active-particle mode (buffers sized by the caller)
+        int32_t *gact = static_cast<int32_t *>(h->group_act.p), *gacts = static_cast<int32_t *>(h->group_act_scan.p);
+        const int32_t *perm = static_cast<const int32_t *>(h->keys_in_alt ? h->vals_alt.p : h->vals.p);
+        k_group_active<<<grid_for(n), kThreads, 0, s>>>(gfirst, cnt + 1, perm, h->active, gact);
+        count_launch();
+        rc = scan_exclusive_i32(gact, gacts, n, cnt + 1, h->temp.p, s);
+        if (rc) return rc;
+        k_active_list<<<grid_for(n), kThreads, 0, s>>>(gact, gacts, cnt + 1,
+                                                       static_cast<int32_t *>(h->active_list.p), cnt + 2);
+        count_launch();
+    }
     return cuda_check(cudaGetLastError(), "build kernels");
 }
 

@@ -53,6 +53,15 @@ struct ph_leaves {
     phpp::DevBuf status;         // uint32 device status word
     phpp::DevBuf temp;           // scan / sort scratch
     bool keys_in_alt = false;
+    // active-particle mode (adaptive time steps): when `active` (caller-order
+    // flags, device) is set, the build lists the groups holding a flagged
+    // particle and the pair builder gives entries to those groups only; the
+    // other groups get empty lists, so the PP kernel sums nothing for them
+    // (and writes zero accelerations) at almost no cost
+    const uint8_t *active = nullptr;
+    phpp::DevBuf group_act;      // int32[n + 1]: group flags
+    phpp::DevBuf group_act_scan; // int32[n + 1]: their exclusive scan
+    phpp::DevBuf active_list;    // int32[n]: the active groups in order; count in counts[2]
 };
 
 struct ph_pairs {

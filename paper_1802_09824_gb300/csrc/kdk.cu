@@ -31,6 +31,7 @@ struct ph_sim {
     int64_t force_passes = 0;
     bool has_mass = false;
     phpp::DevBuf x, p, mass, acc, level, start, next, status;
+    phpp::DevBuf act;             // uint8[n]: particles whose step ends at the next event
     ph_leaves *lv = nullptr;
     ph_pairs *pr = nullptr;
     ph_pm *pm = nullptr;
@@ -111,6 +112,19 @@ __global__ void k_sim_kick(int64_t n, const float *acc, double *p, int32_t *leve
         }
         if (!ka.last) atomicMin(next, s + (ka.T >> k));
     }
+}
+
+// The particles whose step ends at the next event (the tick the kick just
+// found): the only ones whose forces the next force pass must compute.  Like
+// the kick, it does nothing after a pair-list overflow (the flags of the
+// event to redo stay as they are).
+__global__ void k_sim_active(int64_t n, const int32_t *level, const int32_t *start, const int32_t *next, int T,
+                             const uint32_t *guard, uint8_t *act)
+{
+    if (guard && (*guard & ST_CAPACITY)) return;
+    const int t = *next;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        act[i] = start[i] + (T >> level[i]) == t ? 1 : 0;
 }
 
 __global__ void k_sim_drift(int64_t n, double *x, const double *p, double D, double L)
@@ -195,7 +209,7 @@ void sim_release(ph_sim *h)
     h->pm = nullptr;
     h->pr = nullptr;
     h->lv = nullptr;
-    DevBuf *bufs[] = {&h->x, &h->p, &h->mass, &h->acc, &h->level, &h->start, &h->next, &h->status};
+    DevBuf *bufs[] = {&h->x, &h->p, &h->mass, &h->acc, &h->level, &h->start, &h->next, &h->status, &h->act};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -207,6 +221,26 @@ int add_pm(ph_sim *h, cudaStream_t s)
     const int rc = ph_pm_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.n_mesh, static_cast<float *>(h->acc.p),
                                nullptr, 1, s, &h->pm);
     return rc < 0 ? rc : PH_OK;
+}
+
+// From now on the force passes compute forces for the active particles
+// only (Sec. 3.5: a particle's force is needed at the end of its own step):
+// the build lists the groups holding an active particle, the pair builder
+// lists sources for those groups only (the PP kernel passes over the others
+// and writes zeros for them), PM interpolates active particles only.  The
+// kicks read the accelerations of active particles only; at the end of a
+// top step every particle is active.
+int enable_active(ph_sim *h)
+{
+    if (!h->lv) return PH_OK;
+    const size_t N = (size_t)h->n;
+    int rc = ensure(h->lv->group_act, 4 * (N + 1));
+    if (!rc) rc = ensure(h->lv->group_act_scan, 4 * (N + 1));
+    if (!rc) rc = ensure(h->lv->active_list, 4 * N);
+    if (rc) return rc;
+    h->lv->active = static_cast<const uint8_t *>(h->act.p);
+    if (h->pm) pm_set_active(h->pm, static_cast<const uint8_t *>(h->act.p));
+    return PH_OK;
 }
 
 // A full force pass with sizing (host synchronisations): build, a pair list
@@ -230,6 +264,7 @@ int force_pass_sized(ph_sim *h, cudaStream_t s)
     rc = ph_accel(h->x.p, PH_F64, m, h->n, &h->prm, h->kp.g_mode, nullptr, acc, s, &h->lv, &h->pr);
     if (rc < 0) return rc;
     rc = add_pm(h, s);
+    if (!rc) rc = enable_active(h);
     if (rc) return rc;
     rc = ph_graph_create(h->lv, h->pr, h->x.p, PH_F64, m, h->kp.g_mode, nullptr, acc, 0.25, s, &h->graph);
     return rc < 0 ? rc : PH_OK;
@@ -267,6 +302,12 @@ int launch_kick(ph_sim *h, const KickArgs &ka, cudaStream_t s, int32_t *next_hos
                                                         static_cast<int32_t *>(h->level.p),
                                                         static_cast<int32_t *>(h->start.p), nx, guard, ka);
         count_launch();
+        if (!ka.last) {
+            k_sim_active<<<grid_of(h->n), kSimThreads, 0, s>>>(h->n, static_cast<const int32_t *>(h->level.p),
+                                                              static_cast<const int32_t *>(h->start.p), nx, ka.T,
+                                                              guard, static_cast<uint8_t *>(h->act.p));
+            count_launch();
+        }
         rc = cuda_check(cudaGetLastError(), "kick kernel");
         uint32_t st = 0;
         if (!rc) rc = cuda_check(cudaMemcpyAsync(next_host, nx, 4, cudaMemcpyDeviceToHost, s), "read event");
@@ -375,6 +416,7 @@ int ph_sim_create(const double *pos, const double *mom, const float *mass, int64
     if (!rc) rc = ensure(h->level, 4 * N);
     if (!rc) rc = ensure(h->start, 4 * N);
     if (!rc) rc = ensure(h->next, 16);
+    if (!rc) rc = ensure(h->act, N);
     const cudaMemcpyKind kind = cudaMemcpyDefault;
     if (!rc) rc = cuda_check(cudaMemcpyAsync(h->x.p, pos, 24 * N, kind, s), "copy positions");
     if (!rc) rc = cuda_check(cudaMemcpyAsync(h->p.p, mom, 24 * N, kind, s), "copy momenta");

@@ -35,6 +35,7 @@ struct PairArgs {
     float4 *ent;             // fill pass output: offset x, y, z, first source particle (bits)
     uint8_t *ecnt;           // fill pass output: particles in the leaf - 1
     const int32_t *leaf_first;
+    const int32_t *group_list;   // active-particle mode: the groups to list (n_groups points at their count)
     int64_t n_particles;     // mass-centre particle of leaf l: pos_leaf[n_particles + l]
     int64_t cap;
     uint32_t *status;
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
     const unsigned lt = (1u << lane) - 1u;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int ng = *a.n_groups;
-    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps) {
+    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ng; gi += warps) {
+        const int g = a.group_list ? a.group_list[gi] : gi;
         const BoxDev &bx = a.boxes[a.group_box[g]];
         const int ns = bx.nside;
         const int ground = a.group_cell[g] - bx.cell_base;
@@ -207,20 +209,31 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.leaf_r4 = static_cast<const float4 *>(lv->leaf_r4.p);
     a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);
     a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
+    a.group_list = nullptr;
+    if (lv->active) {
+        // only the active groups get entries; the others keep an empty range
+        a.group_list = static_cast<const int32_t *>(lv->active_list.p);
+        a.n_groups = static_cast<const int32_t *>(lv->counts.p) + 2;
+    }
     a.n_particles = lv->n;
     a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
     a.off = static_cast<const int64_t *>(pr->group_off.p);
     a.status = static_cast<uint32_t *>(pr->status.p);
     const int64_t n = lv->n;
     const int grid = 152 * 8;
+    const int32_t *n_all = static_cast<const int32_t *>(lv->counts.p) + 1;
+    if (lv->active) {
+        const int rz = cuda_check(cudaMemsetAsync(a.cnt, 0, 8 * (size_t)(n > 0 ? n : 1), s), "clear counts");
+        if (rz) return rz;
+    }
     k_pairs<false><<<grid, kThreads, 0, s>>>(a);
     count_launch();
-    int rc = scan_exclusive_i64(a.cnt, static_cast<int64_t *>(pr->group_off.p), n, a.n_groups, pr->temp.p, s);
+    int rc = scan_exclusive_i64(a.cnt, static_cast<int64_t *>(pr->group_off.p), n, n_all, pr->temp.p, s);
     if (rc) return rc;
     if (sizing_sync) {
         // total = group_off[n_groups]; read the count then the total
         int32_t ng = 0;
-        rc = cuda_check(cudaMemcpyAsync(&ng, a.n_groups, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy n_groups");
+        rc = cuda_check(cudaMemcpyAsync(&ng, n_all, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy n_groups");
         if (rc) return rc;
         rc = cuda_check(cudaStreamSynchronize(s), "sync n_groups");
         if (rc) return rc;

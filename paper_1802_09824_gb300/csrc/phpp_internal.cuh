@@ -64,6 +64,10 @@ inline float float_at_or_above(double L)
 // Ground level of a box (N_side = 2^g cells of side >= rcut); api.cu.
 int ground_level(double L, double rcut);
 
+// Active-particle mode of a PM handle (pm.cu): interpolate only the
+// particles flagged in `active` (caller order, device; NULL = all).
+void pm_set_active(ph_pm *h, const uint8_t *active);
+
 // Streaming multiprocessors of the current device (persistent grids).
 inline int sm_count()
 {

@@ -47,6 +47,10 @@ struct ph_pm {
     phpp::DevBuf status;     // uint32 device status word
     phpp::DevBuf in_pos, in_mass, acc_tmp, pot_tmp;
     double tab_L = 0.0, tab_rs = -1.0;
+    // active-particle mode (adaptive time steps): when set (caller-order
+    // flags, device), only flagged particles are interpolated; the others
+    // keep their acceleration (every particle is still deposited)
+    const uint8_t *active = nullptr;
 };
 
 namespace phpp {
@@ -219,9 +223,10 @@ __global__ void k_pm_grad(const float *phi, int N, float c_half, float4 *mesh_a)
 
 template <int PT>
 __global__ void k_pm_interp(const void *pos, int64_t n, double L, double inv_dg, int N, const float4 *mesh_a,
-                            float *acc, float *pot, int accumulate)
+                            float *acc, float *pot, int accumulate, const uint8_t *active)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (active && !active[i]) continue;
         const double x = load_coord<PT>(pos, 3 * i), y = load_coord<PT>(pos, 3 * i + 1),
                      z = load_coord<PT>(pos, 3 * i + 2);
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) continue;   // latched by the deposit
@@ -351,6 +356,8 @@ int pm_tables(ph_pm *h, double L, double rs, cudaStream_t s)
 
 }  // namespace
 
+void pm_set_active(ph_pm *h, const uint8_t *active) { h->active = active; }
+
 void pm_free(ph_pm *h)
 {
     pm_release(h);
@@ -468,9 +475,11 @@ int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, con
     float4 *ma = static_cast<float4 *>(h->mesh_a.p);
     k_pm_grad<<<grid_of(cells), kPmThreads, 0, s>>>(mr, N, (float)(-0.5 / dg), ma);
     if (pos_type == PH_F64)
-        k_pm_interp<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate);
+        k_pm_interp<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate,
+                                                              h->active);
     else
-        k_pm_interp<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate);
+        k_pm_interp<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate,
+                                                              h->active);
     count_launch(2);
     rc = cuda_check(cudaGetLastError(), "PM kernels");
     if (!rc && host_acc)
