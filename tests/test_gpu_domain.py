@@ -50,3 +50,53 @@ def test_local_sets_give_the_whole_box_forces(gpu_lib, n_domains):
     assert np.percentile(e, 99) <= P99_TOL
     for h in (pr, lv):
         B.ph_free(h)
+
+
+def _one_rank_nccl(port, q):
+    # one NCCL rank on the one GPU: the exchange (all_to_all_single on device
+    # tensors) and ph_accel on the local set, as every rank of a real run does
+    import os
+    import sys
+    import torch
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
+    from paper_1802_09824_gb300 import binding as BB
+    from paper_1802_09824_gb300 import domain
+    from test_domain import L, RCUT, RS, _particles
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    pos, mass = _particles()
+    prm = BB.make_params(L, 1.0, 1e-3, RS, RCUT, 32)
+    ids = torch.arange(len(pos), dtype=torch.int64, device="cuda")
+    ids_own, acc_own, local = domain.accel_partitioned(torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda(),
+                                                       ids, prm)
+    q.put((ids_own.cpu().numpy(), acc_own.cpu().numpy(), local.n_owned))
+    dist.destroy_process_group()
+
+
+def test_partitioned_call_on_one_nccl_rank(gpu_lib):
+    import os
+    import torch
+    import torch.multiprocessing as mp
+    B = gpu_lib
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_one_rank_nccl, args=(29900 + os.getpid() % 1000, q))
+    p.start()
+    ids, acc, n_owned = q.get(timeout=300)
+    p.join(timeout=60)
+    assert p.exitcode == 0
+    pos, mass = _particles()
+    assert n_owned == len(pos) and np.array_equal(np.sort(ids), np.arange(len(pos)))
+    prm = B.make_params(L, 1.0, 1e-3, RS, RCUT, 32)
+    whole = torch.zeros((len(pos), 3), device="cuda")
+    lv, pr = B.ph_accel(torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda(), prm, B.PH_G_EXACT, None, whole)
+    torch.cuda.synchronize()
+    got = np.empty_like(acc)
+    got[ids] = acc
+    np.testing.assert_array_equal(got, whole.cpu().numpy())      # one rank: the same set, the same bits
+    for h in (pr, lv):
+        B.ph_free(h)
