@@ -3,13 +3,15 @@ FP64 oracle computes one by one (all sources, minimum image, cutoff):
 
 * the 128^3 Zel'dovich lattice in the configuration bench.py times (leaf 32,
   binary levels, Peano-Hilbert keys, 32-particle groups, kernel shape 0,
-  the captured step graph), random targets;
-* the 256^3 NFW mixture (16.8M particles), random targets plus every
+  the captured step graph), 10^4 random targets plus every particle of the
+  8 target groups with the longest source lists;
+* the 256^3 NFW mixture (16.8M particles), 10^4 random targets plus every
   particle of the 8 target groups with the longest source lists (the dense
   halo cores that stress the leaf-pair imbalance);
 * the 512 batched boxes (9.8M particles) in one graph, random targets in 16
   random boxes;
-* the learned factor on the 128^3 lattice against the oracle's FP64 network.
+* the learned factor on the 128^3 lattice against the oracle's FP64 network,
+  10^4 random targets.
 Tolerances are those of the smaller parity tests (helpers.P99_TOL, MAX_TOL;
 the learned path's inference tolerance of tests/test_gpu_mlp.py)."""
 import numpy as np
@@ -49,7 +51,7 @@ def test_zeldovich_128_bench_configuration(gpu_lib):
     torch.cuda.synchronize()
     B.ph_status(pr)
     rng = np.random.default_rng(101)
-    t = np.concatenate([rng.choice(ps.n, 1500, replace=False), _dense_targets(B, lv, pr)])
+    t = np.concatenate([rng.choice(ps.n, 10_000, replace=False), _dense_targets(B, lv, pr)])
     ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=t)
     q, m = check_parity(acc.cpu().numpy()[t], ref)
     print(f"zeldovich 128^3 (bench configuration): p99 {q:.2e} max {m:.2e}")
@@ -70,7 +72,7 @@ def test_nfw_mixture_256_sampled(gpu_lib):
     torch.cuda.synchronize()
     B.ph_status(pr)
     rng = np.random.default_rng(102)
-    t = np.concatenate([rng.choice(ps.n, 600, replace=False), _dense_targets(B, lv, pr)])
+    t = np.concatenate([rng.choice(ps.n, 10_000, replace=False), _dense_targets(B, lv, pr)])
     ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=t)
     q, m = check_parity(acc.cpu().numpy()[t], ref)
     print(f"NFW mixture 256^3: p99 {q:.2e} max {m:.2e} over {t.size} targets")
@@ -123,7 +125,7 @@ def test_learned_factor_128_sampled(gpu_lib):
     lv, pr = B.ph_accel(pos, mass, prm, B.PH_G_LEARNED, m, acc)
     torch.cuda.synchronize()
     rng = np.random.default_rng(104)
-    t = rng.choice(ps.n, 400, replace=False)
+    t = rng.choice(ps.n, 10_000, replace=False)
     ref = force.accel_mlp(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rcut, w.astype(np.float64), targets=t)
     got = acc.cpu().numpy()[t].astype(np.float64)
     am = np.linalg.norm(ref, axis=1)
