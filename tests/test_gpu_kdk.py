@@ -81,15 +81,17 @@ def _rel(got, ref, base):
     return np.linalg.norm(got - ref, axis=1) / np.maximum(den, tau)
 
 
-@pytest.mark.parametrize("clock", [kdk.CLOCK_NEWTON, kdk.CLOCK_LCDM])
-def test_kdk_matches_oracle(gpu_lib, monkeypatch, clock):
+@pytest.mark.parametrize("clock,g_mode", [(kdk.CLOCK_NEWTON, 0), (kdk.CLOCK_LCDM, 0), (kdk.CLOCK_NEWTON, 2)])
+def test_kdk_matches_oracle(gpu_lib, monkeypatch, clock, g_mode):
+    # g_mode 2: the tabulated factor (its error, 5e-6, is far inside the
+    # tolerances below) against the oracle's exact one
     B = gpu_lib
     pos, mom, mass, L = _system()
     n = len(pos)
     eta, max_level, n_mesh = 0.025, 5, 16
     if clock == kdk.CLOCK_NEWTON:
         dt, t0, ck = 0.0196, 0.0, kdk.Clock()
-        kp = B.make_kdk_params(dt, eta, max_level, n_mesh)
+        kp = B.make_kdk_params(dt, eta, max_level, n_mesh, g_mode=g_mode)
     else:
         # the top step in the scale factor whose physical length matches
         # the Newtonian case at a = 0.5 (a H(a) = 0.88 for H0 = 1)
