@@ -30,13 +30,12 @@ struct ph_sim {
     double t = 0.0;
     int64_t force_passes = 0;
     bool has_mass = false;
-    phpp::DevBuf x, p, mass, acc, level, start, next, status;
+    phpp::DevBuf x, p, mass, acc, level, start, next;
     phpp::DevBuf act;             // uint8[n]: particles whose step ends at the next event
     ph_leaves *lv = nullptr;
     ph_pairs *pr = nullptr;
     ph_pm *pm = nullptr;
     ph_graph *graph = nullptr;    // build + pairs + PP captured once (fixed pair capacity)
-    int64_t rebuilds = 0;         // pair lists regrown after a capacity overflow
 };
 
 namespace phpp {
@@ -209,7 +208,7 @@ void sim_release(ph_sim *h)
     h->pm = nullptr;
     h->pr = nullptr;
     h->lv = nullptr;
-    DevBuf *bufs[] = {&h->x, &h->p, &h->mass, &h->acc, &h->level, &h->start, &h->next, &h->status, &h->act};
+    DevBuf *bufs[] = {&h->x, &h->p, &h->mass, &h->acc, &h->level, &h->start, &h->next, &h->act};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -315,7 +314,6 @@ int launch_kick(ph_sim *h, const KickArgs &ka, cudaStream_t s, int32_t *next_hos
         if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "event sync");
         if (rc) return rc;
         if (!(st & ST_CAPACITY)) return PH_OK;
-        h->rebuilds++;
         rc = force_pass_sized(h, s);     // the kick above did nothing: redo the pass, then kick
         if (rc) return rc;
     }
