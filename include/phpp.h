@@ -77,7 +77,11 @@ extern "C" {
  * Parameters of one periodic box.
  *   L         box side (> 0); positions may lie anywhere, they are wrapped.
  *   G         gravitational constant.
- *   eps       Plummer softening (>= 0).
+ *   eps       Plummer softening (>= 0).  The exact kernel evaluates
+ *             (r^2 + eps^2)^(-3/2) in units where rcut is ~1 and floors the
+ *             scaled eps^2 at 1e-12 (so that no FP32 intermediate of a
+ *             coincident pair leaves the normal range): a softening below
+ *             ~1e-6 rcut acts as ~1e-6 rcut.
  *   rs        split scale R_s of Eq. (split) (> 0).
  *   rcut      cutoff radius, 0 < rcut < L/2 (R_cut of Sec. 3.1).
  *   leaf_max  largest number of particles in an octree leaf, 1..256 (the

@@ -166,3 +166,29 @@ def test_count_within_matches_oracle(gpu_lib):
         assert ev >= n + ps.n and st > 0
         B.ph_free(pr)
         B.ph_free(lv)
+
+
+def test_large_box_keeps_relative_precision(gpu_lib):
+    # FP64 positions near 5e4 in a box of side 1e5 with a clump 0.05 across
+    # (mean separation 1.6e-3): FP32 absolute coordinates there are spaced
+    # 4e-3 apart (d_ij would be off by tens of percent); the leaf-relative
+    # FP32 frames keep the usual parity.  The softening stays above the
+    # kernel's floor of ~1e-6 rcut.
+    import torch
+    B = gpu_lib
+    rng = np.random.default_rng(55)
+    L = 1.0e5
+    centre = np.array([51234.567, 40000.123, 33333.3])
+    clump = centre + 0.02 * rng.normal(size=(2000, 3))
+    pos = np.concatenate([rng.random((2000, 3)) * L, clump])
+    mass = np.full(len(pos), 1.0 / len(pos), np.float32)
+    rs = 100.0
+    prm = B.make_params(L, 1.0, 1e-3, rs, 4.5 * rs, 32)
+    acc = torch.zeros((len(pos), 3), device="cuda")
+    lv, pr = B.ph_accel(torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda(), prm, B.PH_G_EXACT, None, acc)
+    torch.cuda.synchronize()
+    ref = force.accel(pos, mass, L, 1.0, 1e-3, rs, 4.5 * rs)
+    q, m = check_parity(acc.cpu().numpy(), ref)
+    print(f"large box: p99 {q:.2e} max {m:.2e}")
+    for h in (pr, lv):
+        B.ph_free(h)
