@@ -192,3 +192,40 @@ def test_large_box_keeps_relative_precision(gpu_lib):
     print(f"large box: p99 {q:.2e} max {m:.2e}")
     for h in (pr, lv):
         B.ph_free(h)
+
+
+@pytest.mark.parametrize("rcut_rs", [6.0, 8.0, 9.0])
+def test_larger_cutoffs_use_higher_degree_factors(gpu_lib, rcut_rs):
+    # rcut / rs = 6, 8, 9 take the degree-12, 14 and 16 polynomials of the
+    # factor (4.5 takes degree 10)
+    rs = 1.25 / 32
+    bp = synth.BoxParams(1.0, 1.0, 1e-3, rs, rcut_rs * rs, 32)
+    base = synth.workload("uniform_small", scale=3000)
+    ps = synth._single(base.pos, base.mass, bp, f"rcut{rcut_rs}")
+    got, lv, pr = gpu_accel(gpu_lib, ps)
+    q, m = check_parity(got, oracle_accel(ps))
+    print(f"rcut = {rcut_rs} rs: p99 {q:.2e} max {m:.2e}")
+    gpu_lib.ph_free(pr)
+    gpu_lib.ph_free(lv)
+
+
+def test_batched_boxes_with_different_constants(gpu_lib):
+    # boxes with their own L, rs, eps and G: the factor constants are read per
+    # box (the kernel instantiation without shared constants), each box
+    # against its own oracle
+    rng = np.random.default_rng(61)
+    boxes, pos, mass = [], [], []
+    for k, (L, rs_frac, eps, G, n) in enumerate([(1.0, 1.25 / 32, 1e-3, 1.0, 1500), (3.0, 1.25 / 20, 5e-3, 0.5, 2000),
+                                                 (0.5, 1.25 / 24, 2e-4, 2.0, 1200)]):
+        rs = rs_frac * L
+        boxes.append(synth.BoxParams(L, G, eps, rs, 4.5 * rs, 32))
+        pos.append((rng.random((n, 3)) * L).astype(np.float32))
+        mass.append(rng.random(n).astype(np.float32) / n)
+    offs = np.concatenate([[0], np.cumsum([len(p) for p in pos])]).astype(np.int64)
+    ps = synth.ParticleSet(np.concatenate(pos), np.concatenate(mass), boxes, offs, "mixed")
+    got, lv, pr = gpu_accel(gpu_lib, ps)
+    for b in range(len(boxes)):
+        sl = ps.box_slice(b)
+        check_parity(got[sl], oracle_accel(ps, box=b), G=boxes[b].G)
+    gpu_lib.ph_free(pr)
+    gpu_lib.ph_free(lv)
