@@ -99,6 +99,57 @@ def test_learned_pp_matches_oracle_with_the_same_network(gpu_lib, trained):
         B.ph_free(x)
 
 
+@pytest.mark.parametrize("gs", [8, 16])
+def test_learned_pp_smaller_groups(gpu_lib, trained, gs):
+    # 16- and 8-particle target groups (2 or 4 lanes per target, each taking
+    # every 2nd or 4th source) with the tensor-core network
+    import torch
+    B = gpu_lib
+    h, w, err, loss = trained
+    ps = synth.workload("uniform_small", scale=3000)
+    bp = ps.boxes[0]
+    m = B.ph_mlp_create(w, bp.rs, bp.rcut, tol=1.0)
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, 0, gs)
+    acc = torch.zeros((ps.n, 3), device="cuda")
+    lv, pr = B.ph_accel(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm, B.PH_G_LEARNED, m,
+                        acc)
+    torch.cuda.synchronize()
+    ref = force.accel_mlp(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rcut, w.astype(np.float64))
+    am = np.linalg.norm(ref, axis=1)
+    e = np.linalg.norm(acc.cpu().numpy().astype(np.float64) - ref, axis=1) / np.maximum(am, 1e-3 * np.median(am))
+    assert np.percentile(e, 99) <= 1e-4 and e.max() <= 1e-3
+    for x in (pr, lv, m):
+        B.ph_free(x)
+
+
+@pytest.mark.parametrize("mode", ["learned", "table"])
+def test_graph_replay_of_other_factors(gpu_lib, trained, mode):
+    # the captured step with the learned or the tabulated factor replays the
+    # direct calls bit for bit
+    import torch
+    B = gpu_lib
+    h, w, err, loss = trained
+    ps = synth.workload("uniform_small", scale=4000)
+    bp = ps.boxes[0]
+    m = B.ph_mlp_create(w, bp.rs, bp.rcut, tol=1.0) if mode == "learned" else None
+    g_mode = B.PH_G_LEARNED if mode == "learned" else B.PH_G_TABLE
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32)
+    pos = torch.from_numpy(ps.pos).cuda()
+    mass = torch.from_numpy(ps.mass).cuda()
+    acc = torch.zeros((ps.n, 3), device="cuda")
+    lv, pr = B.ph_accel(pos, mass, prm, g_mode, m, acc)
+    torch.cuda.synchronize()
+    direct = acc.cpu().numpy().copy()
+    gr = B.ph_graph_create(lv, pr, pos, mass, g_mode, m, acc, headroom=0.2)
+    acc.zero_()
+    B.ph_graph_launch(gr)
+    torch.cuda.synchronize()
+    B.ph_status(pr)
+    np.testing.assert_array_equal(acc.cpu().numpy(), direct)
+    for x in (gr, pr, lv) + ((m,) if m is not None else ()):
+        B.ph_free(x)
+
+
 def test_exact_path_judges_the_network(gpu_lib, trained):
     import torch
     B = gpu_lib
