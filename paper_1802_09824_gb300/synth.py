@@ -124,7 +124,7 @@ def zeldovich_lattice(n_side: int, params: BoxParams, seed: int, rms_cells: floa
     psi = []
     for K in (KX, KY, KZ):
         psi_k = 1j * K * delta_k / k2
-        psi.append(np.fft.irfftn(psi_k, s=white.shape))
+        psi.append(np.fft.irfftn(psi_k, s=white.shape, axes=(0, 1, 2)))
     psi = np.stack([p.ravel() for p in psi], axis=1)
     rms = math.sqrt(float(np.mean(np.sum(psi * psi, axis=1))))
     psi *= rms_cells * a / rms
