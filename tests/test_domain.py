@@ -160,3 +160,23 @@ def test_gloo_ranks_exchange_own_particles_and_ghosts(world):
         loc = force.accel(lpos, lmass, L, 1.0, 1e-3, RS, RCUT, targets=np.arange(n_own))
         ref = glob.acc[lid[:n_own]]
         assert np.max(np.abs(loc.acc - ref)) <= 1e-12 * np.max(glob.abs_sum[lid[:n_own]])
+
+
+def test_domain_calls_reject_bad_arguments():
+    pos, _ = _particles(200)
+    with pytest.raises(B.PhError) as ei:
+        B.ph_domain_cells(pos, B.make_params(1.0, 1.0, 1e-3, 0.2, 0.6, 32))      # rcut >= L/2
+    assert ei.value.code == B.PH_ERR_ARG
+    bad = pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(B.PhError) as ei:
+        B.ph_domain_cells(bad, _params())
+    assert ei.value.code == B.PH_ERR_NONFINITE
+    counts = np.ones(8 ** 3, np.int64)
+    for ns, kk, nd in ((6, B.PH_KEY_HILBERT, 2), (8, 7, 2), (8, B.PH_KEY_MORTON, 0)):
+        with pytest.raises(B.PhError) as ei:
+            B.ph_domain_partition(counts[: ns ** 3], ns, kk, nd)
+        assert ei.value.code == B.PH_ERR_ARG
+    with pytest.raises(B.PhError) as ei:
+        B.ph_domain_halo(np.zeros(27, np.int32), 3, 0)                            # not a power of two
+    assert ei.value.code == B.PH_ERR_ARG
