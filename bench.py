@@ -55,14 +55,18 @@ UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice
-# with leaf_max 32, binary levels, 32-particle groups, kernel shape 0 and
-# Peano-Hilbert keys, from the ncu capture summarised in
-# profiles/pp_exact_zeldovich64.md: that capture is the same configuration on
-# the 64^3 lattice (25.33 MB per launch), scaled by the evaluated pairs of a
-# full launch (3.447e9 / 4.488e8); None for any other configuration, or once
-# the kernel has changed since the capture.
-PP_TRAFFIC_BYTES = 25.331e6 * 3.447e9 / 4.48774e8
-PP_TRAFFIC_CONFIG = ("zeldovich_128", 0, 32, 1, 0, 32, 1)   # workload, scale, leaf_max, levels, variant, group, key
+# with binary levels, 32-particle groups, kernel shape 0 and Peano-Hilbert
+# keys, per leaf size, from the ncu captures summarised in
+# profiles/pp_exact_zeldovich64.md: those captures are the same configuration
+# on the 64^3 lattice (25.33 MB per launch with leaf_max 32, 34.95 MB with
+# 16), scaled by the evaluated pairs of a full launch (3.447e9 / 4.48774e8);
+# None for any other configuration, or once the kernel has changed since the
+# captures.
+_PAIRS_RATIO = 3.447e9 / 4.48774e8
+PP_TRAFFIC = {   # (workload, scale, leaf_max, levels, variant, group, key) -> bytes
+    ("zeldovich_128", 0, 32, 1, 0, 32, 1): 25.331e6 * _PAIRS_RATIO,
+    ("zeldovich_128", 0, 16, 1, 0, 32, 1): (34.940160e6 + 5376) * _PAIRS_RATIO,
+}
 
 
 def _env_int(k, d):
@@ -615,8 +619,8 @@ def run_ours(args, rank, world, local_rank):
     peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                    # TFLOP/s
     achieved = computed * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": PP_TRAFFIC_BYTES if (args.workload, args.scale, prm.leaf_max, prm.level_bits or 1, prm.pp_variant,
-                                             prm.group_size or 32, prm.key_kind) == PP_TRAFFIC_CONFIG else None,
+            "traffic": PP_TRAFFIC.get((args.workload, args.scale, prm.leaf_max, prm.level_bits or 1, prm.pp_variant,
+                                       prm.group_size or 32, prm.key_kind)),
             "kernel": "k_pp (exact factor)", "flops_per_interaction": FLOPS_PER_INTERACTION,
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
     if clk and clk.get("sm_mhz"):
