@@ -199,3 +199,31 @@ def test_pm_plus_pp_matches_ewald_many_bodies():
     # without the long-range part the sum is far off: the test discriminates
     e0 = np.linalg.norm(sr - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert np.median(e0) > 0.3
+
+
+def test_pm_converges_with_the_mesh_at_second_order():
+    # R_s fixed, mesh refined 32 -> 64 -> 128 (R_s = 1.25, 2.5, 5 cells): the
+    # discretisation error of PM + PP against Ewald at r = 2 R_s falls about
+    # fourfold per halving of the cell (CIC, the 3-point Laplacian and the
+    # central difference are all second order)
+    L = 1.0
+    rs = 1.25 / 32
+    rng = np.random.default_rng(12)
+    pairs = []
+    for _ in range(6):
+        x0 = rng.random(3)
+        u = rng.normal(size=3)
+        pairs.append((x0, x0 + u / np.linalg.norm(u) * 2 * rs))
+    med = []
+    for n in (32, 64, 128):
+        errs = []
+        for x0, x1 in pairs:
+            pos = np.array([x0, x1])
+            mass = np.array([1e-12, 1.0])
+            lr = pm.accel(pos, mass, L, 1.0, rs, n, targets=[0]).acc[0]
+            sr = force.accel(pos, mass, L, 1.0, 0.0, rs, 4.5 * rs, targets=np.array([0])).acc[0]
+            ew = ewald_accel(x1 - x0, L)
+            errs.append(np.linalg.norm(lr + sr - ew) / np.linalg.norm(ew))
+        med.append(np.median(errs))
+    assert med[2] < 6e-3
+    assert med[0] / med[1] > 2.5 and med[1] / med[2] > 3.0
