@@ -101,12 +101,15 @@ extern "C" {
  *             registers, more warps).  Same results.
  *   theta     opening criterion of the tree part (Sec. 3.3), in [0, 1):
  *             0 (default) = every leaf pair by PP (the exact short-range
- *             sum); theta > 0 = a leaf whose box centre is at distance R >
- *             (A + B) / theta from the target group's box centre (A, B the
- *             largest box widths; this implies the second criterion
- *             B / (R - A) < theta) acts on the group as one particle of the
- *             leaf's mass at its mass centre, still with the split factor
- *             and the cutoff.  Tree leaves only (no interior nodes).
+ *             sum); theta > 0 = a leaf for which both opening angles
+ *             theta_1 = (A + B) / R and theta_2 = B / (R - A) are below
+ *             theta (A the target group's largest box width, B the leaf's,
+ *             R the distance of the box centres) acts on the group as one
+ *             particle of the leaf's mass at its mass centre, still with
+ *             the split factor and the cutoff.  Decided in FP32 from the
+ *             stored boxes (rounded outwards to FP32), so a pair within a
+ *             few FP32 roundings of the threshold may go either way.  Tree
+ *             leaves only (no interior nodes).
  */
 typedef struct ph_params {
     double  L;

@@ -131,18 +131,21 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                 const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
                 const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
                 acc = px * px + py * py + pz * pz < rf2;
-                // tree part: accepted as one mass-centre particle when the box
-                // centres are further apart than (A + B) / theta (A, B the
-                // largest box widths), decided in FP32 with every rounding fixed
+                // tree part (Sec. 3.3): accepted as one mass-centre particle
+                // when both opening angles are below theta, theta_1 = (A + B)/R
+                // and theta_2 = B/(R - A) (A the group's largest box width, B
+                // the leaf's, R the distance of the box centres), i.e. R >
+                // (A + B)/theta and R > A + B/theta, compared as squares
                 if (acc && bx.c_acc < INFINITY) {
-                    const float ex = __fsub_rn(__fadd_rn(lc.x, __fmul_rn((float)odx, hc)), gc.x);
-                    const float ey = __fsub_rn(__fadd_rn(lc.y, __fmul_rn((float)ody, hc)), gc.y);
-                    const float ez = __fsub_rn(__fadd_rn(lc.z, __fmul_rn((float)odz, hc)), gc.z);
-                    const float R2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                    const float A = __fmul_rn(2.f, fmaxf(fmaxf(gh.x, gh.y), gh.z));
-                    const float Bw = __fmul_rn(2.f, fmaxf(fmaxf(lh.x, lh.y), lh.z));
-                    const float D = __fmul_rn(__fadd_rn(A, Bw), bx.c_acc);
-                    mono = R2 > __fmul_rn(D, D);
+                    const float ex = (lc.x + odx * hc) - gc.x;
+                    const float ey = (lc.y + ody * hc) - gc.y;
+                    const float ez = (lc.z + odz * hc) - gc.z;
+                    const float R2 = ex * ex + ey * ey + ez * ez;
+                    const float A = 2.f * fmaxf(fmaxf(gh.x, gh.y), gh.z);
+                    const float Bw = 2.f * fmaxf(fmaxf(lh.x, lh.y), lh.z);
+                    const float D1 = (A + Bw) * bx.c_acc;
+                    const float D2 = A + Bw * bx.c_acc;
+                    mono = R2 > D1 * D1 && R2 > D2 * D2;
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc);
