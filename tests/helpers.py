@@ -18,21 +18,21 @@ P99_TOL = 1e-5
 MAX_TOL = 1e-3
 
 
-def rel_errors(got, ref_res, G=1.0):
+def rel_errors(got, ref_res):
     ref = ref_res.acc
     amag = np.linalg.norm(ref, axis=1)
     tau = 1e-3 * np.median(amag) if amag.size else 0.0
     den = np.maximum(amag, tau)
     diff = np.linalg.norm(np.asarray(got, np.float64) - ref, axis=1)
     # a pair within FP32 rounding of rcut may be kept or dropped: its whole
-    # term is an admissible difference
-    slack = np.abs(G) * ref_res.near_abs
+    # term (G included, as the oracle sums it) is an admissible difference
+    slack = ref_res.near_abs
     e = np.maximum(diff - slack, 0.0) / np.where(den > 0, den, 1.0)
     return e
 
 
-def check_parity(got, ref_res, G=1.0, p99=P99_TOL, emax=MAX_TOL):
-    e = rel_errors(got, ref_res, G)
+def check_parity(got, ref_res, p99=P99_TOL, emax=MAX_TOL):
+    e = rel_errors(got, ref_res)
     if e.size == 0:
         return 0.0, 0.0
     q = float(np.percentile(e, 99))
