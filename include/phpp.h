@@ -334,7 +334,7 @@ typedef struct ph_pm_view {
 int ph_pm_get_view(const ph_pm *pm, ph_pm_view *out);
 
 /* ------------------------------------------------------------ adaptive KDK
- * The time integration of Sec. 3.5 driving repeated force calls: the
+ * The time integration of Sec. 3.4 driving repeated force calls: the
  * symplectic Drift x += p int dt/a^2 and Kick p += a_grav int dt/a, applied
  * as Kick-Drift-Kick, with every particle's step the top step halved until
  * it is below t_acc = sqrt(2 eta eps / |a|) (Gadget-2's criterion; the
@@ -549,8 +549,11 @@ int ph_mlp_loss_grad(const float *weights, const float *z0, const float *target,
  *   d_pos   [n*3] device float32 positions (any real coordinates; wrapped).
  *   d_mass  [n]   device float32 masses, or NULL for 1/n each.
  *   n       0 .. PH_NOALLOC_MAX_N; larger n returns PH_ERR_ARG.
- *   params  as for ph_build_leaves; L/rcut must give at most
- *           PH_NOALLOC_MAX_CELLS ground cells (else PH_ERR_ARG).
+ *   params  as for ph_build_leaves, with three limits (else PH_ERR_ARG):
+ *           theta must be 0 (every leaf pair by PP), group_size 0 or 32,
+ *           and L/rcut must give at most PH_NOALLOC_MAX_CELLS ground cells.
+ *           The key depth, factor polynomial and box constants are those
+ *           ph_build_leaves derives for the same box.
  *   d_acc   [n*3] device float32 output, caller order.
  * The call synchronises `stream` once before returning.  PH_ERR_CAPACITY
  * means the leaf-pair list needed more than PH_NOALLOC_PAIRS_PER_PARTICLE

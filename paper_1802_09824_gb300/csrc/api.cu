@@ -145,7 +145,20 @@ static int key_bits_per_axis(int n_boxes)
     return (63 - box_bits) / 3;
 }
 
-static int poly_degree_for(double U)
+// Key bits per axis: enough for cells ~64 times finer than the mean spacing
+// of the most populated box (deeper cells never hold more than leaf_max
+// particles outside strong clustering; cells that do are cut into runs),
+// capped by the 63-bit key and at least 4 bits below the ground grid.  The
+// sort takes ceil((3 T + box bits) / 8) passes: 5 for 2^21 particles in one
+// box.
+int key_bits_for(int64_t nmax, int gmax, int n_boxes)
+{
+    int lg = 0;
+    while ((int64_t)1 << (3 * lg) < nmax) lg++;     // ceil(log2(cbrt(nmax)))
+    return std::min(key_bits_per_axis(n_boxes), std::max(lg + 6, gmax + 4));
+}
+
+int poly_degree_for(double U)
 {
     if (U <= 2.3) return 10;
     if (U <= 3.05) return 12;
@@ -175,6 +188,33 @@ static int check_params(const ph_params &p, int b)
     if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
         return fail(PH_ERR_ARG, "box %d: rcut/rs = %g above the supported 9.2", b, p.rcut / p.rs);
     return PH_OK;
+}
+
+void fill_box(BoxDev &bx, const ph_params &p, int key_bits, int poly_degree, int64_t n_box, int cell_base,
+              int32_t first, int group_size)
+{
+    memset(&bx, 0, sizeof bx);
+    bx.L = p.L;
+    bx.L_up = float_at_or_above(p.L);
+    bx.c_acc = p.theta > 0 ? (float)(1.0 / p.theta) : INFINITY;
+    bx.g = ground_level(p.L, p.rcut);
+    bx.b = key_bits - bx.g;
+    bx.nside = 1 << bx.g;
+    bx.S = std::ldexp(1.0, key_bits) / p.L;
+    bx.h = p.L / bx.nside;
+    set_softening(bx, p.G, p.eps, p.rcut);
+    bx.rcut2 = (float)(p.rcut * p.rcut);
+    const double rf = p.rcut * (1.0 + 3e-5);
+    bx.rfilt2 = (float)(rf * rf);
+    bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
+    bx.c_t = (float)(2.0 / p.rcut);
+    bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
+    bx.mass_default = n_box > 0 ? (float)(1.0 / (double)n_box) : 0.f;
+    bx.cell_base = cell_base;
+    bx.first = first;
+    bx.n = (int32_t)n_box;
+    bx.group_size = group_size;
+    fit_factor_poly(p.rcut / (2.0 * p.rs), poly_degree, bx.poly);
 }
 
 static void free_leaves(ph_leaves *h)
@@ -230,22 +270,13 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->n = n;
     h->n_boxes = nb;
     {
-        // key bits per axis: enough for cells ~64 times finer than the mean
-        // spacing of the most populated box (deeper cells never hold more
-        // than leaf_max particles outside strong clustering; cells that do
-        // are cut into runs), capped by the 63-bit key and at least 4 bits
-        // below the ground grid.  The sort takes ceil((3 T + box bits) / 8)
-        // passes: 5 for 2^21 particles in one box.
         int64_t nmax = 1;
         int gmax = 0;
         for (int b = 0; b < nb; b++) {
             nmax = std::max<int64_t>(nmax, box_offsets[b + 1] - box_offsets[b]);
             gmax = std::max(gmax, ground_level(params[b].L, params[b].rcut));
         }
-        int lg = 0;
-        while ((int64_t)1 << (3 * lg) < nmax) lg++;     // ceil(log2(cbrt(nmax)))
-        const int cap = key_bits_per_axis(nb);
-        h->key_bits = std::min(cap, std::max(lg + 6, gmax + 4));
+        h->key_bits = key_bits_for(nmax, gmax, nb);
     }
     h->max_leaf = params[0].leaf_max;
     h->key_kind = params[0].key_kind;
@@ -265,30 +296,9 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     for (int b = 0; b < nb; b++) {
         const ph_params &p = params[b];
         BoxDev &bx = h->boxes_host[b];
-        memset(&bx, 0, sizeof bx);
-        bx.L = p.L;
-        bx.L_up = float_at_or_above(p.L);
-        bx.c_acc = p.theta > 0 ? (float)(1.0 / p.theta) : INFINITY;
         if (p.theta > 0) h->tree_leaves = true;
-        bx.g = ground_level(p.L, p.rcut);
-        bx.b = h->key_bits - bx.g;
-        bx.nside = 1 << bx.g;
-        bx.S = std::ldexp(1.0, h->key_bits) / p.L;
-        bx.h = p.L / bx.nside;
-        set_softening(bx, p.G, p.eps, p.rcut);
-        bx.rcut2 = (float)(p.rcut * p.rcut);
-        double rf = p.rcut * (1.0 + 3e-5);
-        bx.rfilt2 = (float)(rf * rf);
-        bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
-        bx.c_t = (float)(2.0 / p.rcut);
-        bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
-        const int64_t nbx = box_offsets[b + 1] - box_offsets[b];
-        bx.mass_default = nbx > 0 ? (float)(1.0 / (double)nbx) : 0.f;
-        bx.cell_base = cells;
-        bx.first = (int32_t)box_offsets[b];
-        bx.n = (int32_t)nbx;
-        bx.group_size = h->group_size;
-        fit_factor_poly(p.rcut / (2.0 * p.rs), deg, bx.poly);
+        fill_box(bx, p, h->key_bits, deg, box_offsets[b + 1] - box_offsets[b], cells, (int32_t)box_offsets[b],
+                 h->group_size);
         cells += bx.nside * bx.nside * bx.nside;
         bf[b] = (int32_t)box_offsets[b];
     }

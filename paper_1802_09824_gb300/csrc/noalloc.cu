@@ -24,7 +24,6 @@ namespace phpp {
 int build_leaves_device(ph_leaves *h, const void *pos, int pos_type, const float *mass, cudaStream_t s);
 int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool sizing_sync);
 int pp_exact_device(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, cudaStream_t s);
-void fit_factor_poly(double U, int deg, float *coef);
 }  // namespace phpp
 
 using namespace phpp;
@@ -57,7 +56,8 @@ int scratch_address(void **out)
     return PH_OK;
 }
 
-// Bump carver over the scratch array (256-byte aligned slices).
+// Bump carver over the scratch array (256-byte aligned slices); with base
+// NULL it only measures.
 struct Carver {
     char *base;
     size_t used = 0;
@@ -72,108 +72,18 @@ struct Carver {
             b.bytes = 0;
             return;
         }
-        b.p = base + at;
+        b.p = base ? base + at : nullptr;
         b.bytes = bytes;
         used = at + bytes;
     }
 };
 
-int ground_level_of(double L, double rcut)
+// Carve every buffer of the step for n particles and `cells` ground cells.
+void carve(Carver &c, ph_leaves &lv, ph_pairs &pr, int64_t n, int cells)
 {
-    int g = 0;
-    while (g < kGroundMax && L / (double)(1 << (g + 1)) >= rcut) g++;
-    return g;
-}
-
-int degree_for(double U)
-{
-    if (U <= 2.3) return 10;
-    if (U <= 3.05) return 12;
-    if (U <= 4.05) return 14;
-    if (U <= 4.6) return 16;
-    return -1;
-}
-
-}  // namespace
-
-extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t n, const ph_params *params,
-                                float *d_acc, void *stream)
-{
-    if (!params) return fail(PH_ERR_ARG, "params must not be NULL");
-    if (n < 0 || n > PH_NOALLOC_MAX_N)
-        return fail(PH_ERR_ARG, "ph_accel_noalloc: n = %lld outside 0..%d (the fixed scratch holds at most %d particles)",
-                    (long long)n, PH_NOALLOC_MAX_N, PH_NOALLOC_MAX_N);
-    const ph_params &p = *params;
-    if (!(std::isfinite(p.L) && p.L > 0) || !(std::isfinite(p.rs) && p.rs > 0) || !(std::isfinite(p.eps) && p.eps >= 0) ||
-        !std::isfinite(p.G) || !(std::isfinite(p.rcut) && p.rcut > 0))
-        return fail(PH_ERR_ARG, "ph_accel_noalloc: L, rs, rcut must be finite and > 0, eps >= 0, G finite");
-    if (!(p.rcut < 0.5 * p.L)) return fail(PH_ERR_RCUT_GE_HALF_L, "rcut %g >= L/2 %g", p.rcut, 0.5 * p.L);
-    if (p.leaf_max < 1 || p.leaf_max > kMaxLeaf) return fail(PH_ERR_ARG, "leaf_max must be 1..%d", kMaxLeaf);
-    if (p.theta != 0) return fail(PH_ERR_ARG, "ph_accel_noalloc: theta must be 0 (every leaf pair by PP)");
-    if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT) return fail(PH_ERR_ARG, "unknown key_kind");
-    if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "group_size must be 0 or 32");
-    if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3) return fail(PH_ERR_ARG, "level_bits must be 0, 1 or 3");
-    if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "pp_variant must be 0 or 1");
-    const int deg = degree_for(p.rcut / (2.0 * p.rs));
-    if (deg < 0) return fail(PH_ERR_ARG, "rcut/rs = %g above the supported 9.2", p.rcut / p.rs);
-    if (n == 0) return PH_OK;
-    if (!d_pos || !d_acc || !is_device_ptr(d_pos) || !is_device_ptr(d_acc) || (d_mass && !is_device_ptr(d_mass)))
-        return fail(PH_ERR_ARG, "ph_accel_noalloc: pos, mass and acc must be device memory");
-    const int g = ground_level_of(p.L, p.rcut);
-    const int nside = 1 << g;
-    const int cells = nside * nside * nside;
-    if (cells > PH_NOALLOC_MAX_CELLS)
-        return fail(PH_ERR_ARG, "ph_accel_noalloc: L/rcut gives %d ground cells, above the fixed %d", cells,
-                    PH_NOALLOC_MAX_CELLS);
-
-    void *base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-
-    // one box: the same constants ph_build_leaves derives
-    BoxDev bx;
-    memset(&bx, 0, sizeof bx);
-    const int T = 21;
-    bx.L = p.L;
-    bx.L_up = float_at_or_above(p.L);
-    bx.c_acc = INFINITY;   // every leaf pair by PP (theta must be 0 here)
-    bx.g = g;
-    bx.b = T - g;
-    bx.nside = nside;
-    bx.S = std::ldexp(1.0, T) / p.L;
-    bx.h = p.L / nside;
-    set_softening(bx, p.G, p.eps, p.rcut);
-    bx.rcut2 = (float)(p.rcut * p.rcut);
-    const double rf = p.rcut * (1.0 + 3e-5);
-    bx.rfilt2 = (float)(rf * rf);
-    bx.c_v = (float)(4.0 / (p.rcut * p.rcut));
-    bx.c_t = (float)(2.0 / p.rcut);
-    bx.c_e = (float)(-1.4426950408889634 / (4.0 * p.rs * p.rs));
-    bx.mass_default = (float)(1.0 / (double)n);
-    bx.cell_base = 0;
-    bx.first = 0;
-    bx.n = (int32_t)n;
-    bx.group_size = 32;
-    fit_factor_poly(p.rcut / (2.0 * p.rs), deg, bx.poly);
-    const int32_t box_first[2] = {0, (int32_t)n};
-
-    ph_leaves lv;   // host descriptors only; every buffer points into the scratch
-    ph_pairs pr;
-    lv.n = n;
-    lv.n_boxes = 1;
-    lv.n_cells = cells;
-    lv.key_bits = T;
-    lv.group_size = 32;
-    lv.poly_degree = deg;
-    lv.max_leaf = p.leaf_max;
-    lv.key_kind = p.key_kind;
-    lv.level_bits = p.level_bits ? p.level_bits : 1;
-    lv.pp_variant = p.pp_variant == 1 ? 1 : 0;
     const size_t N = (size_t)n;
-    Carver c{static_cast<char *>(base)};
     c.take(lv.boxes, sizeof(BoxDev));
-    c.take(lv.box_first, sizeof box_first);
+    c.take(lv.box_first, 2 * sizeof(int32_t));
     c.take(lv.keys, 8 * N);
     c.take(lv.keys_alt, 8 * N);
     c.take(lv.vals, 4 * N);
@@ -210,11 +120,82 @@ extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t
     c.take(pr.work, 64);
     c.take(pr.status, 16);
     c.take(pr.temp, tscan);
-    const int64_t cap = (int64_t)PH_NOALLOC_PAIRS_PER_PARTICLE * n;
-    c.take(pr.entries, 16 * (size_t)cap);
-    c.take(pr.ecount, (size_t)cap);
+    const size_t cap = (size_t)PH_NOALLOC_PAIRS_PER_PARTICLE * N;
+    c.take(pr.entries, 16 * cap);
+    c.take(pr.ecount, cap);
+}
+
+}  // namespace
+
+extern "C" int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t n, const ph_params *params,
+                                float *d_acc, void *stream)
+{
+    if (!params) return fail(PH_ERR_ARG, "params must not be NULL");
+    if (n < 0 || n > PH_NOALLOC_MAX_N)
+        return fail(PH_ERR_ARG, "ph_accel_noalloc: n = %lld outside 0..%d (the fixed scratch holds at most %d particles)",
+                    (long long)n, PH_NOALLOC_MAX_N, PH_NOALLOC_MAX_N);
+    const ph_params &p = *params;
+    if (!(std::isfinite(p.L) && p.L > 0) || !(std::isfinite(p.rs) && p.rs > 0) || !(std::isfinite(p.eps) && p.eps >= 0) ||
+        !std::isfinite(p.G) || !(std::isfinite(p.rcut) && p.rcut > 0))
+        return fail(PH_ERR_ARG, "ph_accel_noalloc: L, rs, rcut must be finite and > 0, eps >= 0, G finite");
+    if (!(p.rcut < 0.5 * p.L)) return fail(PH_ERR_RCUT_GE_HALF_L, "rcut %g >= L/2 %g", p.rcut, 0.5 * p.L);
+    if (p.leaf_max < 1 || p.leaf_max > kMaxLeaf) return fail(PH_ERR_ARG, "leaf_max must be 1..%d", kMaxLeaf);
+    if (p.theta != 0) return fail(PH_ERR_ARG, "ph_accel_noalloc: theta must be 0 (every leaf pair by PP)");
+    if (p.key_kind != PH_KEY_MORTON && p.key_kind != PH_KEY_HILBERT) return fail(PH_ERR_ARG, "unknown key_kind");
+    if (p.group_size != 0 && p.group_size != 32) return fail(PH_ERR_ARG, "group_size must be 0 or 32");
+    if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3) return fail(PH_ERR_ARG, "level_bits must be 0, 1 or 3");
+    if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "pp_variant must be 0 or 1");
+    const int deg = poly_degree_for(p.rcut / (2.0 * p.rs));
+    if (deg < 0) return fail(PH_ERR_ARG, "rcut/rs = %g above the supported 9.2", p.rcut / p.rs);
+    const int g = ground_level(p.L, p.rcut);
+    const int nside = 1 << g;
+    const int cells = nside * nside * nside;
+    if (cells > PH_NOALLOC_MAX_CELLS)
+        return fail(PH_ERR_ARG, "ph_accel_noalloc: L/rcut gives %d ground cells, above the fixed %d", cells,
+                    PH_NOALLOC_MAX_CELLS);
+    {
+        // the documented maximum must fit the array whatever n this call has,
+        // so a buffer that grows breaks every call, not only the largest ones
+        ph_leaves lm;
+        ph_pairs pm;
+        Carver dry{nullptr};
+        carve(dry, lm, pm, PH_NOALLOC_MAX_N, PH_NOALLOC_MAX_CELLS);
+        if (dry.over)
+            return fail(PH_ERR_CAPACITY, "ph_accel_noalloc: the fixed scratch (%u bytes) is smaller than its "
+                        "documented maximum of %d particles and %d cells needs", PH_NOALLOC_SCRATCH_BYTES,
+                        PH_NOALLOC_MAX_N, PH_NOALLOC_MAX_CELLS);
+    }
+    if (n == 0) return PH_OK;
+    if (!d_pos || !d_acc || !is_device_ptr(d_pos) || !is_device_ptr(d_acc) || (d_mass && !is_device_ptr(d_mass)))
+        return fail(PH_ERR_ARG, "ph_accel_noalloc: pos, mass and acc must be device memory");
+
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // one box with the constants and key depth ph_build_leaves derives for it
+    const int T = key_bits_for(n, g, 1);
+    BoxDev bx;
+    fill_box(bx, p, T, deg, n, 0, 0, kDefaultGroup);
+    const int32_t box_first[2] = {0, (int32_t)n};
+
+    ph_leaves lv;   // host descriptors only; every buffer points into the scratch
+    ph_pairs pr;
+    lv.n = n;
+    lv.n_boxes = 1;
+    lv.n_cells = cells;
+    lv.key_bits = T;
+    lv.group_size = kDefaultGroup;
+    lv.poly_degree = deg;
+    lv.max_leaf = p.leaf_max;
+    lv.key_kind = p.key_kind;
+    lv.level_bits = p.level_bits ? p.level_bits : 1;
+    lv.pp_variant = p.pp_variant == 1 ? 1 : 0;
+    Carver c{static_cast<char *>(base)};
+    carve(c, lv, pr, n, cells);
     if (c.over) return fail(PH_ERR_CAPACITY, "ph_accel_noalloc: fixed scratch too small for n = %lld", (long long)n);
-    pr.capacity = cap;
+    pr.capacity = (int64_t)PH_NOALLOC_PAIRS_PER_PARTICLE * n;
     pr.fixed_capacity = true;
 
     // the array keeps the previous call's contents: clear what must start at zero

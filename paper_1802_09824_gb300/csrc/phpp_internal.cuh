@@ -64,6 +64,19 @@ inline float float_at_or_above(double L)
 // Ground level of a box (N_side = 2^g cells of side >= rcut); api.cu.
 int ground_level(double L, double rcut);
 
+// Key bits per axis for n_boxes boxes of at most nmax particles whose finest
+// ground level is gmax; api.cu.
+int key_bits_for(int64_t nmax, int gmax, int n_boxes);
+
+// Degree of the factor polynomial for U = rcut / (2 rs), -1 if unsupported;
+// api.cu.
+int poly_degree_for(double U);
+
+// The device record of one box (constants of the build, the pair builder and
+// the PP kernel) from its parameters; api.cu.
+void fill_box(BoxDev &bx, const struct ph_params &p, int key_bits, int poly_degree, int64_t n_box, int cell_base,
+              int32_t first, int group_size);
+
 // Active-particle mode of a PM handle (pm.cu): interpolate only the
 // particles flagged in `active` (caller order, device; NULL = all).
 void pm_set_active(ph_pm *h, const uint8_t *active);
