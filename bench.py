@@ -52,20 +52,18 @@ UNIT = "interactions/s"
 # inverse cube); t = sqrt(r^2) 2/rcut - 1 1 FFMA; degree-10 Horner 10 FFMA;
 # ex2 argument 1 FMUL; f 1 FMUL; w 2 FMUL; accumulation 3 FFMA
 #   ->  3 FADD + 7 FMUL + 17 FFMA = 44 flop.
+# The ncu counters of one 128^3 launch (sm__sass_thread_inst_executed_op_
+# {fadd2,fmul2,ffma2}_pred_on) give 44.13 flop per evaluated pair for the
+# packed pair arithmetic (the excess is the padded lanes of partial runs).
 FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
-# DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice
-# with binary levels, 32-particle groups, kernel shape 0 and Peano-Hilbert
-# keys, per leaf size, from the ncu captures summarised in
-# profiles/pp_exact_zeldovich64.md: those captures are the same configuration
-# on the 64^3 lattice (25.33 MB per launch with leaf_max 32, 34.95 MB with
-# 16), scaled by the evaluated pairs of a full launch (3.447e9 / 4.48774e8);
-# None for any other configuration, or once the kernel has changed since the
-# captures.
-_PAIRS_RATIO = 3.447e9 / 4.48774e8
+# DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice,
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# k_pp launch of this benchmark's configuration: leaf_max 32, binary levels,
+# kernel shape 0, 32-particle groups, Peano-Hilbert keys.  None for any other
+# configuration, or once the kernel has changed since the capture.
 PP_TRAFFIC = {   # (workload, scale, leaf_max, levels, variant, group, key) -> bytes
-    ("zeldovich_128", 0, 32, 1, 0, 32, 1): 25.331e6 * _PAIRS_RATIO,
-    ("zeldovich_128", 0, 16, 1, 0, 32, 1): (34.940160e6 + 5376) * _PAIRS_RATIO,
+    ("zeldovich_128", 0, 32, 1, 0, 32, 1): 194206720 + 18382080,
 }
 
 

@@ -1,4 +1,4 @@
-"""Adaptive Kick-Drift-Kick stepping (Sec. 3.5), oracle side.
+"""Adaptive Kick-Drift-Kick stepping (Sec. 3.4), oracle side.
 
 Test infrastructure only (see the package docstring).  Plain numpy in
 float64, written from the paper's description:
@@ -131,7 +131,7 @@ class Sim:
         return step_levels(self.acc, self.dt / self.clock.step_scale(t), self.eta, self.eps_step, self.max_level)
 
     def top_step(self):
-        """One top step of length dt (Sec. 3.5's KDK with halved steps)."""
+        """One top step of length dt (Sec. 3.4's KDK with halved steps)."""
         T = 1 << self.max_level
         h = self.dt / T
         t0 = self.t

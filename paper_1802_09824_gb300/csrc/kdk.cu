@@ -1,4 +1,4 @@
-// Adaptive Kick-Drift-Kick block steps (Sec. 3.5) driving the force calls.
+// Adaptive Kick-Drift-Kick block steps (Sec. 3.4) driving the force calls.
 //
 // Drift x += p D(t1; t2), Kick p += a K(t1; t2) with D = int dt / a^2 and
 // K = int dt / a (Newtonian clock: both t2 - t1).  One top step of length dt
@@ -223,7 +223,7 @@ int add_pm(ph_sim *h, cudaStream_t s)
 }
 
 // From now on the force passes compute forces for the active particles
-// only (Sec. 3.5: a particle's force is needed at the end of its own step):
+// only (Sec. 3.4: a particle's force is needed at the end of its own step):
 // the build lists the groups holding an active particle, the pair builder
 // lists sources for those groups only (the PP kernel passes over the others
 // and writes zeros for them), PM interpolates active particles only.  The

@@ -162,7 +162,7 @@ def test_adaptive_levels_follow_fine_reference():
 
 
 def three_body(dt, eta, max_level, steps):
-    """Sec. 3.5's test of KDK under the force split: a close binary (two
+    """Sec. 3.4's test of KDK under the force split: a close binary (two
     masses 0.01 at separation 0.05 < R_s, bound by the short-range force)
     on an orbit of radius 1 > R_cut around a unit mass (the long-range PM
     force), in a periodic box of side 4 with a 32^3 mesh.  Returns the
