@@ -532,6 +532,39 @@ int ph_mlp_get(const ph_mlp *mlp, float *weights, float *max_rel_err, float *las
 int ph_mlp_loss_grad(const float *weights, const float *z0, const float *target, int64_t n, float *grad,
                      float *loss, void *stream);
 
+/*
+ * Saving and loading a trained network (no counterpart in the paper, which
+ * tabulates g instead: this is the checkpoint of the learned factor).
+ *
+ * File layout, all little-endian, 1348 bytes:
+ *   bytes  0..7     magic "PHMLP\0\0\1"
+ *   8..11           uint32 format version (1)
+ *   12..15          uint32 parameter count (321)
+ *   16..23          float64 rs the network was trained for
+ *   24..31          float64 rcut
+ *   32..35          float32 validated max |g_hat/g - 1| at save time
+ *   36..39          float32 last training loss
+ *   40..43          int32   training steps done
+ *   44..47          uint32  reserved (0)
+ *   48..1331        float32 weights[321] in the order of ph_mlp_create
+ *   1332..1339      uint64  FNV-1a hash of bytes 0..1331
+ *   1340..1347      uint64  reserved (0)
+ *
+ * ph_mlp_file_write / ph_mlp_file_read are host only (no GPU needed).
+ * Read errors: PH_ERR_ARG for a missing or short file, a wrong magic,
+ * version or count, or a hash that does not match (a damaged file).
+ * ph_mlp_save writes the weights of a handle (synchronising the device);
+ * ph_mlp_load reads a file into a new handle whose error is validated anew
+ * on the device against the exact factor, accepted up to `tol` as in
+ * ph_mlp_create.  The caller owns the returned handle (ph_free).
+ */
+int ph_mlp_file_write(const char *path, const float *weights, double rs, double rcut, float max_rel_err,
+                      float last_loss, int32_t steps);
+int ph_mlp_file_read(const char *path, float *weights, double *rs, double *rcut, float *max_rel_err,
+                     float *last_loss, int32_t *steps);
+int ph_mlp_save(const ph_mlp *mlp, const char *path);
+int ph_mlp_load(const char *path, float tol, void *stream, ph_mlp **mlp);
+
 /* ------------------------------------------------------------ no allocation
  * ph_accel_noalloc -- the whole step (ph_accel with the exact factor) for
  * one small box, without allocating anything.
@@ -574,6 +607,18 @@ int ph_accel_noalloc(const float *d_pos, const float *d_mass, int64_t n, const p
 /* Kernel launches the library has issued so far in this process (all
  * threads); differences around a region count the launches inside it. */
 int64_t ph_launch_counter(void);
+
+/*
+ * Testing hook for failure paths (no counterpart in the paper): after k
+ * more device allocations made by the library (k = 0: the next one), one
+ * fails exactly as if the device were out of memory (the old buffer is
+ * released, PH_ERR_OOM is returned); k < 0 turns the hook off.  One shot:
+ * the hook turns itself off after the failure.  A call that fails this way
+ * leaves a fresh handle unmade (nothing leaks) and an existing handle
+ * invalid (PH_ERR_STATE from every call that would read it) until it is
+ * built again successfully.
+ */
+void ph_debug_fail_allocation(int64_t k);
 
 #ifdef __cplusplus
 }

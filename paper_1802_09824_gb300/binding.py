@@ -121,6 +121,14 @@ _SIGS = {
                       ctypes.c_int),
     "ph_mlp_get": ([_VP, _VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "ph_mlp_loss_grad": ([_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_float), _VP], ctypes.c_int),
+    "ph_mlp_file_write": ([ctypes.c_char_p, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_int32], ctypes.c_int),
+    "ph_mlp_file_read": ([ctypes.c_char_p, _VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                          ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "ph_mlp_save": ([_VP, ctypes.c_char_p], ctypes.c_int),
+    "ph_mlp_load": ([ctypes.c_char_p, ctypes.c_float, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "ph_debug_fail_allocation": ([ctypes.c_int64], None),
     "ph_graph_create": ([_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP,
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
@@ -350,6 +358,40 @@ def ph_mlp_get(mlp):
     l = ctypes.c_float(0)
     _check(lib().ph_mlp_get(mlp.ptr, _ptr(w), ctypes.byref(e), ctypes.byref(l)))
     return w, e.value, l.value
+
+
+def ph_mlp_file_write(path, weights, rs, rcut, max_rel_err=0.0, last_loss=0.0, steps=0):
+    """Write a network file (host only; layout in phpp.h)."""
+    w = np.ascontiguousarray(np.asarray(weights, np.float32))
+    assert w.size == PH_MLP_PARAMS
+    _check(lib().ph_mlp_file_write(os.fsencode(path), _ptr(w), float(rs), float(rcut), float(max_rel_err),
+                                   float(last_loss), int(steps)))
+
+
+def ph_mlp_file_read(path):
+    """(weights float32[321], rs, rcut, max_rel_err, last_loss, steps) of a network file (host only)."""
+    w = np.zeros(PH_MLP_PARAMS, np.float32)
+    rs, rcut = ctypes.c_double(0), ctypes.c_double(0)
+    err, loss = ctypes.c_float(0), ctypes.c_float(0)
+    steps = ctypes.c_int32(0)
+    _check(lib().ph_mlp_file_read(os.fsencode(path), _ptr(w), ctypes.byref(rs), ctypes.byref(rcut), ctypes.byref(err),
+                                  ctypes.byref(loss), ctypes.byref(steps)))
+    return w, rs.value, rcut.value, err.value, loss.value, steps.value
+
+
+def ph_mlp_save(mlp, path):
+    _check(lib().ph_mlp_save(mlp.ptr, os.fsencode(path)))
+
+
+def ph_mlp_load(path, tol=0.0, stream=None):
+    out = ctypes.c_void_p(None)
+    _check(lib().ph_mlp_load(os.fsencode(path), float(tol), _stream(stream), ctypes.byref(out)))
+    return Handle(out.value)
+
+
+def ph_debug_fail_allocation(k):
+    """Make the k-th next device allocation of the library fail (k < 0: off)."""
+    lib().ph_debug_fail_allocation(int(k))
 
 
 def ph_mlp_loss_grad(weights, z0, target, stream=None):

@@ -92,6 +92,10 @@ int cuda_check(cudaError_t e, const char *what)
     return fail(PH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Testing hook (ph_debug_fail_allocation): the number of device allocations
+// still allowed before one fails as if the device were out of memory; -1 off.
+static std::atomic<long long> g_fail_after{-1};
+
 int ensure(DevBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
@@ -99,6 +103,10 @@ int ensure(DevBuf &b, size_t bytes)
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
+    long long k = g_fail_after.load();
+    while (k >= 0 && !g_fail_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) return fail(PH_ERR_OOM, "cudaMalloc(%zu bytes) failed: injected allocation failure", bytes);
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -217,6 +225,49 @@ void fill_box(BoxDev &bx, const ph_params &p, int key_bits, int poly_degree, int
     fit_factor_poly(p.rcut / (2.0 * p.rs), poly_degree, bx.poly);
 }
 
+int check_built(const ph_leaves *lv, const ph_pairs *pr)
+{
+    if (!lv->valid) return fail(PH_ERR_STATE, "the leaves handle holds no completed build (a build failed)");
+    if (pr && !pr->valid) return fail(PH_ERR_STATE, "the pairs handle holds no completed list (ph_leaf_pairs failed)");
+    if (pr && pr->leaves_generation != lv->generation)
+        return fail(PH_ERR_STATE, "the pair list was made for an earlier build of the leaves: call ph_leaf_pairs");
+    return PH_OK;
+}
+
+static void fp_mix(uint64_t &h, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) {
+        h ^= (v >> (8 * i)) & 0xffu;
+        h *= 1099511628211ull;
+    }
+}
+
+uint64_t buffers_fingerprint(const ph_leaves *h, const ph_pairs *p)
+{
+    uint64_t f = 1469598103934665603ull;
+    const DevBuf *lb[] = {&h->boxes, &h->box_first, &h->keys, &h->keys_alt, &h->vals, &h->vals_alt, &h->xw,
+                          &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag, &h->leaf_scan,
+                          &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4, &h->leaf_h4,
+                          &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext,
+                          &h->work, &h->table, &h->group_cell, &h->group_box, &h->pos_leaf, &h->pos_group,
+                          &h->cell_leaf_first, &h->counts, &h->status, &h->temp, &h->group_act, &h->group_act_scan,
+                          &h->active_list};
+    for (const DevBuf *b : lb) {
+        fp_mix(f, (uint64_t)(uintptr_t)b->p);
+        fp_mix(f, (uint64_t)b->bytes);
+    }
+    fp_mix(f, (uint64_t)h->n);
+    if (p) {
+        const DevBuf *pb[] = {&p->group_cnt, &p->group_off, &p->entries, &p->ecount, &p->work, &p->status, &p->temp};
+        for (const DevBuf *b : pb) {
+            fp_mix(f, (uint64_t)(uintptr_t)b->p);
+            fp_mix(f, (uint64_t)b->bytes);
+        }
+        fp_mix(f, (uint64_t)p->capacity);
+    }
+    return f;
+}
+
 static void free_leaves(ph_leaves *h)
 {
     DevBuf *bufs[] = {&h->boxes, &h->box_first, &h->in_pos, &h->in_mass, &h->keys, &h->keys_alt, &h->vals,
@@ -267,6 +318,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         fresh = true;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->valid = false;   // until this build completes
     h->n = n;
     h->n_boxes = nb;
     {
@@ -389,6 +441,8 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         }
         return rc;
     }
+    h->valid = true;
+    h->generation++;
     *leaves = h;
     return PH_OK;
 }
@@ -436,10 +490,15 @@ int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity)
         p = new (std::nothrow) ph_pairs();
         if (!p) return fail(PH_ERR_OOM, "host allocation failed");
     }
+    // the entries may move: the list has to be built (again) before use
+    p->valid = false;
     int rc = ensure(p->entries, (size_t)(capacity > 0 ? capacity : 1) * sizeof(float4));
     if (!rc) rc = ensure(p->ecount, (size_t)(capacity > 0 ? capacity : 1));
     if (rc) {
-        if (fresh) delete p;
+        if (fresh) {
+            free_pairs(p);
+            delete p;
+        }
         return rc;
     }
     p->capacity = capacity;
@@ -454,11 +513,14 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
     if (!pairs) return fail(PH_ERR_ARG, "pairs must not be NULL");
     ph_pairs *p = *pairs;
     if (p && p->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "handle is not a ph_pairs");
+    int rc0 = check_built(leaves, nullptr);
+    if (rc0) return rc0;
     bool fresh = !p;
     if (fresh) {
         p = new (std::nothrow) ph_pairs();
         if (!p) return fail(PH_ERR_OOM, "host allocation failed");
     }
+    p->valid = false;   // until this list completes
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t N = (size_t)(leaves->n > 0 ? leaves->n : 1);
     int rc = 0;
@@ -484,6 +546,8 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
         return rc;
     }
     p->built_from = leaves;
+    p->leaves_generation = leaves->generation;
+    p->valid = true;
     p->last_stream = s;
     *pairs = p;
     return PH_OK;
@@ -495,6 +559,10 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
     if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
     if (pairs && pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    {
+        const int rb = check_built(leaves, pairs);
+        if (rb) return rb;
+    }
     if (g_mode != PH_G_EXACT && g_mode != PH_G_LEARNED && g_mode != PH_G_TABLE)
         return fail(PH_ERR_ARG, "unknown g_mode %d", g_mode);
     if (g_mode == PH_G_LEARNED && (!mlp || mlp->kind != KIND_MLP))
@@ -610,6 +678,10 @@ int ph_status(const void *handle)
 int ph_leaves_get_view(const ph_leaves *h, ph_leaves_view *out)
 {
     if (!h || h->kind != KIND_LEAVES || !out) return fail(PH_ERR_ARG, "bad arguments");
+    {
+        const int rb = check_built(h, nullptr);
+        if (rb) return rb;
+    }
     int32_t cnt[2] = {0, 0};
     int rc = cuda_check(cudaMemcpyAsync(cnt, h->counts.p, 8, cudaMemcpyDeviceToHost, h->last_stream), "read counts");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(h->last_stream), "view sync");
@@ -641,6 +713,10 @@ int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
 {
     if (!p || p->kind != KIND_PAIRS || !out || !p->built_from) return fail(PH_ERR_ARG, "bad arguments");
     const ph_leaves *lv = p->built_from;
+    {
+        const int rb = check_built(lv, p);
+        if (rb) return rb;
+    }
     int32_t ng = 0;
     int rc = cuda_check(cudaMemcpyAsync(&ng, static_cast<const int32_t *>(lv->counts.p) + 1, 4,
                                         cudaMemcpyDeviceToHost, p->last_stream),
@@ -667,6 +743,10 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
     if (!leaves || leaves->kind != KIND_LEAVES || !pairs || pairs->kind != KIND_PAIRS || !n_within)
         return fail(PH_ERR_ARG, "bad arguments");
     if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    {
+        const int rb = check_built(leaves, pairs);
+        if (rb) return rb;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     *n_within = 0;
     if (leaves->n == 0) return PH_OK;
@@ -684,6 +764,8 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
 }
 
 int64_t ph_launch_counter(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+void ph_debug_fail_allocation(int64_t k) { g_fail_after.store(k < 0 ? -1 : (long long)k); }
 
 int ph_pp_counters(const void *handle, int64_t *interactions, int64_t *staged)
 {

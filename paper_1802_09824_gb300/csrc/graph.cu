@@ -36,6 +36,7 @@ struct ph_graph {
     int64_t n = 0;
     ph_leaves *leaves = nullptr;
     ph_pairs *pairs = nullptr;
+    uint64_t fingerprint = 0;     // the handles' buffers at capture (replays need the same)
 };
 
 using namespace phpp;
@@ -57,6 +58,10 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     if (!leaves || leaves->kind != KIND_LEAVES || (pairs && pairs->kind != KIND_PAIRS) || !out)
         return fail(PH_ERR_ARG, "ph_graph_create: leaves and out must be valid, pairs valid or NULL");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
+    {
+        const int rb = check_built(leaves, pairs);
+        if (rb) return rb;
+    }
     if (!pairs && g_mode != PH_G_EXACT) return fail(PH_ERR_ARG, "ph_graph_create: the direct mode is exact only");
     if (!pairs && leaves->tree_leaves) return fail(PH_ERR_ARG, "ph_graph_create: the tree part needs a pair list");
     if (g_mode == PH_G_TABLE) {
@@ -78,7 +83,10 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
             int rc = cuda_check(cudaStreamSynchronize(caller), "sync before growing");
             if (!rc) rc = ensure(pairs->entries, (size_t)want * sizeof(float4));
             if (!rc) rc = ensure(pairs->ecount, (size_t)want);
-            if (rc) return rc;
+            if (rc) {
+                pairs->valid = false;   // the entries are gone
+                return rc;
+            }
             pairs->capacity = want;
         }
         pairs->fixed_capacity = true;
@@ -124,6 +132,7 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
     g->n = leaves->n;
     g->leaves = leaves;
     g->pairs = pairs;
+    g->fingerprint = buffers_fingerprint(leaves, pairs);
     leaves->last_stream = caller;
     if (pairs) pairs->last_stream = caller;
     *out = g;
@@ -136,6 +145,11 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
 int ph_graph_launch(ph_graph *g, void *stream)
 {
     if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
+    // the capture holds the handles' buffer addresses: a rebuild that moved
+    // or dropped any of them (larger n, a failed build) ends the graph's use
+    if (!g->leaves->valid || (g->pairs && !g->pairs->valid) ||
+        buffers_fingerprint(g->leaves, g->pairs) != g->fingerprint)
+        return fail(PH_ERR_STATE, "the handles' buffers changed since the capture: create a new graph");
     int rc = cuda_check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "graph launch");
     if (!rc) count_launch((int)g->kernels);
     return rc;

@@ -8,6 +8,11 @@
 struct ph_leaves {
     uint32_t kind = phpp::KIND_LEAVES;
     cudaStream_t last_stream = nullptr;
+    // valid: the last build completed, so the buffers hold a tree (a build
+    // that fails part-way, e.g. out of memory, leaves the handle invalid
+    // until the next successful build); generation counts successful builds
+    bool valid = false;
+    uint64_t generation = 0;
     int64_t n = 0;
     int32_t n_boxes = 0;
     int32_t n_cells = 0;
@@ -67,6 +72,11 @@ struct ph_leaves {
 struct ph_pairs {
     uint32_t kind = phpp::KIND_PAIRS;
     cudaStream_t last_stream = nullptr;
+    // valid: the last ph_leaf_pairs completed; leaves_generation: the build
+    // of built_from the list was made for (a later build of the leaves makes
+    // the list stale)
+    bool valid = false;
+    uint64_t leaves_generation = 0;
     int64_t capacity = 0;        // entries
     bool fixed_capacity = false;
     int64_t n_pairs = 0;         // host copy (valid after sizing sync)
@@ -81,3 +91,15 @@ struct ph_pairs {
     phpp::DevBuf temp;
     phpp::DevBuf acc_tmp;        // float[3n] when the caller passes host memory
 };
+
+namespace phpp {
+// Refuses a leaves handle without a completed build and a pairs handle that
+// is incomplete or made for another build (PH_ERR_STATE), so no kernel ever
+// reads buffers that a failed or newer build left behind.
+int check_built(const ph_leaves *lv, const ph_pairs *pr);
+
+// A fingerprint of the device buffers of a leaves (and pairs) handle: their
+// addresses and sizes.  A captured graph holds these addresses; it may only
+// be replayed while the fingerprint is unchanged.
+uint64_t buffers_fingerprint(const ph_leaves *lv, const ph_pairs *pr);
+}  // namespace phpp
