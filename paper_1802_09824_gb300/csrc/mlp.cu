@@ -12,6 +12,7 @@
 // Validation evaluates the trained network exactly as the learned PP kernel
 // does (warp-level BF16 tensor-core MMAs) on a dense grid of r in [0, rcut)
 // and records the largest relative deviation from the exact factor.
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -330,6 +331,44 @@ void mlp_free(ph_mlp *h)
 
 using namespace phpp;
 
+// ---- the network file (layout in phpp.h): fixed little-endian fields
+// written byte by byte, so the file is the same on every host.
+namespace {
+constexpr size_t kMlpFileBytes = 1348, kMlpHashed = 1332;
+const unsigned char kMlpMagic[8] = {'P', 'H', 'M', 'L', 'P', 0, 0, 1};
+
+void put_le(unsigned char *b, uint64_t v, int nbytes)
+{
+    for (int i = 0; i < nbytes; i++) b[i] = (unsigned char)(v >> (8 * i));
+}
+
+uint64_t get_le(const unsigned char *b, int nbytes)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < nbytes; i++) v |= (uint64_t)b[i] << (8 * i);
+    return v;
+}
+
+template <typename T, typename U>
+U bits_of(T x)
+{
+    static_assert(sizeof(T) == sizeof(U), "size");
+    U u;
+    memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+uint64_t fnv1a(const unsigned char *b, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; i++) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+}  // namespace
+
 extern "C" {
 
 int ph_mlp_create(const float *weights, double rs, double rcut, float tol, void *stream, ph_mlp **mlp)
@@ -480,6 +519,81 @@ int ph_mlp_get(const ph_mlp *h, float *weights, float *max_rel_err, float *last_
     }
     if (max_rel_err) *max_rel_err = h->max_rel_err;
     if (last_loss) *last_loss = h->last_loss;
+    return PH_OK;
+}
+
+
+int ph_mlp_file_write(const char *path, const float *weights, double rs, double rcut, float max_rel_err,
+                      float last_loss, int32_t steps)
+{
+    if (!path || !weights) return fail(PH_ERR_ARG, "path and weights must not be NULL");
+    unsigned char b[kMlpFileBytes];
+    memset(b, 0, sizeof b);
+    memcpy(b, kMlpMagic, 8);
+    put_le(b + 8, 1, 4);
+    put_le(b + 12, kMlpParams, 4);
+    put_le(b + 16, bits_of<double, uint64_t>(rs), 8);
+    put_le(b + 24, bits_of<double, uint64_t>(rcut), 8);
+    put_le(b + 32, bits_of<float, uint32_t>(max_rel_err), 4);
+    put_le(b + 36, bits_of<float, uint32_t>(last_loss), 4);
+    put_le(b + 40, (uint32_t)steps, 4);
+    for (int e = 0; e < kMlpParams; e++) put_le(b + 48 + 4 * e, bits_of<float, uint32_t>(weights[e]), 4);
+    put_le(b + kMlpHashed, fnv1a(b, kMlpHashed), 8);
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(PH_ERR_ARG, "cannot open %s for writing", path);
+    const size_t w = fwrite(b, 1, sizeof b, f);
+    const int closed = fclose(f);
+    if (w != sizeof b || closed != 0) return fail(PH_ERR_ARG, "cannot write %s", path);
+    return PH_OK;
+}
+
+int ph_mlp_file_read(const char *path, float *weights, double *rs, double *rcut, float *max_rel_err, float *last_loss,
+                     int32_t *steps)
+{
+    if (!path || !weights) return fail(PH_ERR_ARG, "path and weights must not be NULL");
+    unsigned char b[kMlpFileBytes + 1];
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(PH_ERR_ARG, "cannot open %s", path);
+    const size_t got = fread(b, 1, sizeof b, f);
+    fclose(f);
+    if (got != kMlpFileBytes) return fail(PH_ERR_ARG, "%s: %zu bytes, a network file has %zu", path, got, kMlpFileBytes);
+    if (memcmp(b, kMlpMagic, 8) != 0) return fail(PH_ERR_ARG, "%s is not a network file (magic)", path);
+    if (get_le(b + 8, 4) != 1) return fail(PH_ERR_ARG, "%s: unknown format version %u", path, (unsigned)get_le(b + 8, 4));
+    if (get_le(b + 12, 4) != (uint64_t)kMlpParams) return fail(PH_ERR_ARG, "%s: parameter count is not 321", path);
+    if (get_le(b + kMlpHashed, 8) != fnv1a(b, kMlpHashed)) return fail(PH_ERR_ARG, "%s: damaged (hash mismatch)", path);
+    for (int e = 0; e < kMlpParams; e++) weights[e] = bits_of<uint32_t, float>((uint32_t)get_le(b + 48 + 4 * e, 4));
+    if (rs) *rs = bits_of<uint64_t, double>(get_le(b + 16, 8));
+    if (rcut) *rcut = bits_of<uint64_t, double>(get_le(b + 24, 8));
+    if (max_rel_err) *max_rel_err = bits_of<uint32_t, float>((uint32_t)get_le(b + 32, 4));
+    if (last_loss) *last_loss = bits_of<uint32_t, float>((uint32_t)get_le(b + 36, 4));
+    if (steps) *steps = (int32_t)(uint32_t)get_le(b + 40, 4);
+    return PH_OK;
+}
+
+int ph_mlp_save(const ph_mlp *h, const char *path)
+{
+    if (!h || h->kind != KIND_MLP) return fail(PH_ERR_ARG, "not a ph_mlp handle");
+    float w[kMlpParams];
+    int rc = cuda_check(cudaMemcpy(w, h->theta.p, sizeof w, cudaMemcpyDeviceToHost), "read weights");
+    if (rc) return rc;
+    return ph_mlp_file_write(path, w, h->rs, h->rcut, h->max_rel_err, h->last_loss, h->steps_done);
+}
+
+int ph_mlp_load(const char *path, float tol, void *stream, ph_mlp **mlp)
+{
+    if (!mlp) return fail(PH_ERR_ARG, "mlp must not be NULL");
+    float w[kMlpParams];
+    double rs = 0, rcut = 0;
+    float err = 0, loss = 0;
+    int32_t steps = 0;
+    int rc = ph_mlp_file_read(path, w, &rs, &rcut, &err, &loss, &steps);
+    if (rc) return rc;
+    ph_mlp *h = nullptr;
+    rc = ph_mlp_create(w, rs, rcut, tol, stream, &h);
+    if (rc) return rc;
+    h->last_loss = loss;
+    h->steps_done = steps;
+    *mlp = h;
     return PH_OK;
 }
 

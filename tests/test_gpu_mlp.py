@@ -220,3 +220,34 @@ def test_what_the_network_gains_over_the_exact_factor(gpu_lib, trained):
     assert np.percentile(e_learn, 99) <= 50 * max(err, 1e-6)
     for x in (pr, lv, m):
         B.ph_free(x)
+
+
+def test_saved_network_loads_to_identical_forces(gpu_lib, trained, tmp_path):
+    """ph_mlp_save / ph_mlp_load: the file keeps every weight bit, the loaded
+    handle is validated anew to the same error, and the learned PP kernel
+    gives bit-identical forces with either handle."""
+    import torch
+    B = gpu_lib
+    h, w, err, loss = trained
+    path = tmp_path / "g.phmlp"
+    B.ph_mlp_save(h, path)
+    w2, rs, rcut, err2, loss2, steps = B.ph_mlp_file_read(path)
+    assert w2.tobytes() == w.tobytes()
+    assert steps == 20_000 and np.float32(err2) == np.float32(err) and np.float32(loss2) == np.float32(loss)
+    m = B.ph_mlp_load(path, tol=1.0)
+    w3, err3, loss3 = B.ph_mlp_get(m)
+    assert w3.tobytes() == w.tobytes() and err3 == err and np.float32(loss3) == np.float32(loss)
+    ps = synth.workload("uniform_small")
+    bp = ps.boxes[0]
+    pos = torch.from_numpy(ps.pos).cuda()
+    mass = torch.from_numpy(ps.mass).cuda()
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32)
+    a1 = torch.zeros((ps.n, 3), device="cuda")
+    a2 = torch.zeros((ps.n, 3), device="cuda")
+    lv, pr = B.ph_accel(pos, mass, prm, B.PH_G_LEARNED, h, a1)
+    B.ph_pp_accel(lv, pr, B.PH_G_LEARNED, m, a2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a1.cpu().numpy(), a2.cpu().numpy())
+    for x in (pr, lv, m):
+        B.ph_free(x)
+
