@@ -11,13 +11,14 @@ FP64 oracle computes one by one (all sources, minimum image, cutoff):
 * the 512 batched boxes (9.8M particles) in one graph, random targets in 16
   random boxes;
 * the learned factor on the 128^3 lattice against the oracle's FP64 network,
-  10^4 random targets.
+  10^4 random targets (inference parity), and, trained to the benchmark's
+  schedule, against the exact FP64 oracle (its 1e-3 force gate).
 Tolerances are those of the smaller parity tests (helpers.P99_TOL, MAX_TOL;
 the learned path's inference tolerance of tests/test_gpu_mlp.py)."""
 import numpy as np
 import pytest
 
-from helpers import check_parity
+from helpers import check_parity, rel_errors
 from oracle import force
 from paper_1802_09824_gb300 import synth
 
@@ -134,3 +135,41 @@ def test_learned_factor_128_sampled(gpu_lib):
     assert np.percentile(e, 99) <= 1e-4 and e.max() <= 1e-3
     for h in (pr, lv, m):
         B.ph_free(h)
+
+
+def test_learned_factor_meets_its_force_gate_at_128(gpu_lib):
+    """The learned factor's accuracy gate at full size: a network trained to
+    the benchmark's schedule (400k Adam steps of 4096 samples, learning rate
+    2e-3 cosine to 1e-6) is accepted by the exact path's validation (no
+    fallback), and the learned forces on the 128^3 lattice in the benchmark
+    configuration are within 1e-3 (p99) of the exact FP64 oracle on 10^4
+    random targets plus every particle of the 8 densest groups."""
+    import warnings
+
+    import torch
+    B = gpu_lib
+    ps = synth.workload("zeldovich_128")
+    bp = ps.boxes[0]
+    tp = B.make_train_params(n_samples=1_000_000, batch=4096, steps=400_000, lr0=2e-3, lr_min=1e-6, tol=1e-3,
+                             seed=2024)
+    m = B.ph_mlp_train(tp, bp.rs, bp.rcut)
+    w, err, loss = B.ph_mlp_get(m)
+    assert err <= 1e-3, f"validated network error {err:.3e}"
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, B.PH_KEY_HILBERT, 32, 1, 0)
+    pos = torch.from_numpy(ps.pos).cuda()
+    mass = torch.from_numpy(ps.mass).cuda()
+    acc = torch.zeros((ps.n, 3), device="cuda")
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")           # a fallback to the exact factor would warn
+        lv, pr = B.ph_accel(pos, mass, prm, B.PH_G_LEARNED, m, acc)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(105)
+    t = np.concatenate([rng.choice(ps.n, 10_000, replace=False), _dense_targets(B, lv, pr)])
+    ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=t)
+    e = rel_errors(acc.cpu().numpy()[t], ref)
+    print(f"learned factor vs exact FP64 oracle at 128^3: p99 {np.percentile(e, 99):.2e} max {e.max():.2e} "
+          f"(network max |g_hat/g - 1| {err:.2e})")
+    assert np.percentile(e, 99) <= 1e-3
+    for h in (pr, lv, m):
+        B.ph_free(h)
+
