@@ -141,8 +141,8 @@ def _gpu_index(local_rank):
     return local_rank
 
 
-def _params(B, bp, leaf_max, key_kind):
-    return B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max or bp.leaf_max, key_kind)
+def _params(B, bp, leaf_max, key_kind, pp_variant=0):
+    return B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max or bp.leaf_max, key_kind, 0, 0, pp_variant)
 
 
 def _oracle_rate(ps, seconds, seed=5):
@@ -505,7 +505,7 @@ def run_ours(args, rank, world, local_rank):
 
     ps = synth.workload(args.workload, scale=args.scale or None)
     bp = ps.boxes[0]
-    prm = _params(B, bp, args.leaf_max, args.key)
+    prm = _params(B, bp, args.leaf_max, args.key, args.pp_variant)
     pos = torch.from_numpy(ps.pos).to(dev)
     mass = torch.from_numpy(ps.mass).to(dev)
     tune_info = None
@@ -687,6 +687,7 @@ def main():
     ap.add_argument("--scale", type=int, default=0, help="side count of a smaller lattice (profiling)")
     ap.add_argument("--leaf-max", type=int, default=0)
     ap.add_argument("--key", type=int, default=0)
+    ap.add_argument("--pp-variant", type=int, default=0, help="PP kernel shape when the autotuner is off")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
