@@ -36,6 +36,53 @@ __device__ __forceinline__ float rcp_sfu(float x)
     return y;
 }
 
+// ---- packed FP32 pairs (f32x2, sm_100+): two values per instruction
+
+typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pair
+
+__device__ __forceinline__ f2_t pk(float lo, float hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f2_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float hi_of(f2_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
+{
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Exact factor f(r) = 2^(r^2 c_e) h(t), t = 2r/rcut - 1 (scalar form of the
 // PP kernel's evaluation).
 __device__ __forceinline__ float exact_factor(float r2, float t, const float *poly, int npoly, float c_e)
@@ -82,6 +129,13 @@ __device__ __forceinline__ float silu_scaled(float z)
     return z * rcp_sfu(1.f + ex2_sfu(z));
 }
 
+// Two units at once: the add and the multiply as packed FP32.
+__device__ __forceinline__ f2_t silu_scaled2(f2_t z)
+{
+    const f2_t den = add2(pk(ex2_sfu(lo_of(z)), ex2_sfu(hi_of(z))), pk(1.f, 1.f));
+    return mul2(z, pk(rcp_sfu(lo_of(den)), rcp_sfu(hi_of(den))));
+}
+
 // Round to BF16 (ties away from zero) with integer operations: the BF16 value
 // in the upper half of an FP32 word.  Keeps the conversion off the SFU pipe.
 __device__ __forceinline__ uint32_t bf16_round_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
@@ -97,10 +151,10 @@ __device__ __forceinline__ uint32_t pack_upper(uint32_t a, uint32_t b) { return 
 // Weights are stored in the scaled units of silu_scaled: W1, b1 and b2
 // times -log2(e), W3 times -ln2 (W2 and b3 unchanged).
 struct MlpLane {
-    float w1[4], b1[4];          // layer 1 for the lane's 4 columns
+    f2_t w1[4], b1[4];           // layer 1 for the lane's 4 columns (each duplicated: rows g, g + 8)
     uint32_t bhi[2][2], blo[2][2];   // W2^T fragments (hi / lo parts), per n-half
     float b2[2][2];              // bias of output columns 8h + 2q, 8h + 2q + 1
-    float w3[2][2];              // W3 of the same columns
+    f2_t w3[2];                  // W3 of the same two columns, per n-half
     float b3;
 };
 
@@ -112,8 +166,8 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
     const int cols[4] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        L.w1[c] = kz * w[cols[c]];
-        L.b1[c] = kz * w[16 + cols[c]];
+        L.w1[c] = pk(kz * w[cols[c]], kz * w[cols[c]]);
+        L.b1[c] = pk(kz * w[16 + cols[c]], kz * w[16 + cols[c]]);
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -128,8 +182,7 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
         L.blo[h][1] = pack_bf16(lo[2], lo[3]);
         L.b2[h][0] = kz * w[288 + 8 * h + 2 * q];
         L.b2[h][1] = kz * w[288 + 8 * h + 2 * q + 1];
-        L.w3[h][0] = ka * w[304 + 8 * h + 2 * q];
-        L.w3[h][1] = ka * w[304 + 8 * h + 2 * q + 1];
+        L.w3[h] = pk(ka * w[304 + 8 * h + 2 * q], ka * w[304 + 8 * h + 2 * q + 1]);
     }
     L.b3 = w[320];
 }
@@ -145,9 +198,11 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t &hi, uin
 
 // The network's factor for the warp's 32 pairs: lane i passes the input
 // z0 = 2r/rcut - 1 of its pair and receives g_hat of its pair.  Layer 1 and
-// both SiLU layers in FP32 on the FMA/SFU pipes; layer 2 as BF16 tensor-core
-// MMAs with FP32 accumulation, activations and weights split into BF16
-// hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16 bits.
+// both SiLU layers in FP32 on the FMA/SFU pipes, two units per packed
+// instruction (the lane's rows g and g + 8 share layer 1's weights; its two
+// columns 2q, 2q + 1 of a row share layer 3's accumulator pair); layer 2 as
+// BF16 tensor-core MMAs with FP32 accumulation, activations and weights split
+// into BF16 hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16 bits.
 __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
 {
     const int lane = threadIdx.x & 31;
@@ -157,38 +212,35 @@ __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
     for (int tile = 0; tile < 2; tile++) {
         const float za = __shfl_sync(0xffffffffu, z0, 16 * tile + g);
         const float zb = __shfl_sync(0xffffffffu, z0, 16 * tile + g + 8);
-        float ha[4], hb[4];
+        const f2_t zab = pk(za, zb);
+        f2_t h[4];   // column c of rows (g, g + 8)
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            ha[c] = silu_scaled(fmaf(L.w1[c], za, L.b1[c]));
-            hb[c] = silu_scaled(fmaf(L.w1[c], zb, L.b1[c]));
-        }
+        for (int c = 0; c < 4; c++) h[c] = silu_scaled2(fma2(L.w1[c], zab, L.b1[c]));
         uint32_t Ahi[4], Alo[4];
-        split_pack(ha[0], ha[1], Ahi[0], Alo[0]);   // row g, cols 2q, 2q+1
-        split_pack(hb[0], hb[1], Ahi[1], Alo[1]);   // row g+8
-        split_pack(ha[2], ha[3], Ahi[2], Alo[2]);   // row g, cols 2q+8, 2q+9
-        split_pack(hb[2], hb[3], Ahi[3], Alo[3]);   // row g+8
-        float ya = 0.f, yb = 0.f;
+        split_pack(lo_of(h[0]), lo_of(h[1]), Ahi[0], Alo[0]);   // row g, cols 2q, 2q+1
+        split_pack(hi_of(h[0]), hi_of(h[1]), Ahi[1], Alo[1]);   // row g+8
+        split_pack(lo_of(h[2]), lo_of(h[3]), Ahi[2], Alo[2]);   // row g, cols 2q+8, 2q+9
+        split_pack(hi_of(h[2]), hi_of(h[3]), Ahi[3], Alo[3]);   // row g+8
+        f2_t ya = 0ull, yb = 0ull;   // rows g and g + 8: (even column, odd column) partial sums
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            float d[4] = {L.b2[h][0], L.b2[h][1], L.b2[h][0], L.b2[h][1]};
-            mma_bf16(d, Alo, L.bhi[h][0], L.bhi[h][1]);
-            mma_bf16(d, Ahi, L.blo[h][0], L.blo[h][1]);
-            mma_bf16(d, Ahi, L.bhi[h][0], L.bhi[h][1]);
-            ya = fmaf(L.w3[h][0], silu_scaled(d[0]), ya);
-            ya = fmaf(L.w3[h][1], silu_scaled(d[1]), ya);
-            yb = fmaf(L.w3[h][0], silu_scaled(d[2]), yb);
-            yb = fmaf(L.w3[h][1], silu_scaled(d[3]), yb);
+        for (int hh = 0; hh < 2; hh++) {
+            float d[4] = {L.b2[hh][0], L.b2[hh][1], L.b2[hh][0], L.b2[hh][1]};
+            mma_bf16(d, Alo, L.bhi[hh][0], L.bhi[hh][1]);
+            mma_bf16(d, Ahi, L.blo[hh][0], L.blo[hh][1]);
+            mma_bf16(d, Ahi, L.bhi[hh][0], L.bhi[hh][1]);
+            ya = fma2(L.w3[hh], silu_scaled2(pk(d[0], d[1])), ya);
+            yb = fma2(L.w3[hh], silu_scaled2(pk(d[2], d[3])), yb);
         }
-        ya += __shfl_xor_sync(0xffffffffu, ya, 1);
-        ya += __shfl_xor_sync(0xffffffffu, ya, 2);
-        yb += __shfl_xor_sync(0xffffffffu, yb, 1);
-        yb += __shfl_xor_sync(0xffffffffu, yb, 2);
-        // pair p = 16 tile + rho is lane p; rows rho < 8 are held as ya, others
-        // as yb, by the quad 4 (rho % 8) .. 4 (rho % 8) + 3
+        float sa = lo_of(ya) + hi_of(ya), sb = lo_of(yb) + hi_of(yb);
+        sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+        sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+        sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+        sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+        // pair p = 16 tile + rho is lane p; rows rho < 8 are held as sa, others
+        // as sb, by the quad 4 (rho % 8) .. 4 (rho % 8) + 3
         const int rho = lane & 15;
-        const float va = __shfl_sync(0xffffffffu, ya, 4 * (rho & 7));
-        const float vb = __shfl_sync(0xffffffffu, yb, 4 * (rho & 7));
+        const float va = __shfl_sync(0xffffffffu, sa, 4 * (rho & 7));
+        const float vb = __shfl_sync(0xffffffffu, sb, 4 * (rho & 7));
         if ((lane >> 4) == tile) out = (rho < 8 ? va : vb) + L.b3;
     }
     return out;

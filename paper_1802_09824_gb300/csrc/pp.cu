@@ -42,7 +42,6 @@ constexpr int kBlocks0 = PHPP_PP_BLOCKS0;
 constexpr int kBlocks1 = PHPP_PP_BLOCKS1;
 constexpr int kJBuf = 256;      // staged sources per warp (even)
 
-typedef unsigned long long f2_t;   // two FP32 values in one 64-bit register pair
 
 // Constants of one box, each duplicated into both halves of a pair.
 struct PairConsts {
@@ -95,52 +94,6 @@ struct Kahan3 {
         y = pz - cz; t = sz + y; cz = (t - sz) - y; sz = t;
     }
 };
-
-// ---- packed FP32 pairs (f32x2, sm_100+): two sources per instruction
-
-__device__ __forceinline__ f2_t pk(float lo, float hi)
-{
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lo_of(f2_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo;
-}
-__device__ __forceinline__ float hi_of(f2_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return hi;
-}
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b)
-{
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b)
-{
-    f2_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b)
-{
-    f2_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
-{
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
 
 // Two sources (A = x0 x1 y0 y1, B = z0 z1 m0 m1) against one target: add
 // m_j f(r) d / (r^2 + eps^2)^{3/2} into the pair accumulators.
