@@ -229,37 +229,103 @@ __device__ __forceinline__ void sum_buffer_table(const float4 *A, const float4 *
     }
 }
 
-// Learned factor: one source per lane and step (the network is evaluated
-// warp-wide on the tensor cores, so every lane takes part in every step),
-// runs of 16 steps per Kahan add.
+// Learned factor.  The network is evaluated warp-wide (32 pairs per call on
+// the tensor cores), and only pairs within R_cut need it: each lane takes
+// its next source each step, and the pairs with 0 < r^2 < R_cut^2 are
+// appended (ballot order) to a per-warp queue of their separation, mass and
+// r^2; whenever the queue holds 32 pairs, lane k evaluates queue entry k
+// (softened inverse cube, network, weight) and writes the entry's force back
+// into its slot, and every lane adds the forces of the entries it owns in
+// slot order (a deterministic order), then the remaining entries move to the
+// front.  Pairs beyond R_cut, the self pair and coincident pairs contribute
+// exactly zero and are not queued.
+constexpr int kLQ = 64;   // queue slots per warp (at most 31 pending + 32 new)
+struct LearnedQueue {
+    float *qx, *qy, *qz, *qm, *qr;   // per-warp slots in shared memory
+    int n = 0;                       // queued entries (warp-uniform)
+    unsigned long long own = 0;      // slots this lane's entries occupy
+};
+
+// Evaluate the first `ne` (<= 32) queue entries and add their forces to their
+// owners' run sums.
+__device__ __forceinline__ void learned_flush(LearnedQueue &q, int ne, int lane, float eps2, float c_v,
+                                              const MlpLane &L, float &px, float &py, float &pz)
+{
+    __syncwarp();
+    const bool on = lane < ne;
+    const float dx = on ? q.qx[lane] : 0.f, dy = on ? q.qy[lane] : 0.f, dz = on ? q.qz[lane] : 0.f;
+    const float mj = on ? q.qm[lane] : 0.f, r2 = on ? q.qr[lane] : 0.f;
+    const float x = r2 + eps2;
+    const float y = rsqrt_sfu(x);
+    const float y2 = y * y;
+    const float y3 = y2 * y;
+    const float inv3 = fmaf(y3, fmaf(x * -1.5f, y2, 1.5f), y3);
+    const float t = sqrt_sfu(r2 * c_v) - 1.f;
+    const float gh = mlp_warp_eval(t, L);
+    const float w = on ? (mj * gh) * inv3 : 0.f;
+    __syncwarp();
+    q.qx[lane] = w * dx;
+    q.qy[lane] = w * dy;
+    q.qz[lane] = w * dz;
+    __syncwarp();
+    unsigned m32 = (unsigned)q.own & (ne == 32 ? 0xffffffffu : ((1u << ne) - 1u));
+    while (m32) {
+        const int b = __ffs(m32) - 1;
+        m32 &= m32 - 1u;
+        px += q.qx[b];
+        py += q.qy[b];
+        pz += q.qz[b];
+    }
+    __syncwarp();
+    // the entries behind the evaluated ones move to the front
+    const int rest = q.n - ne;
+    if (lane < rest) {
+        const float a0 = q.qx[ne + lane], a1 = q.qy[ne + lane], a2 = q.qz[ne + lane];
+        const float a3 = q.qm[ne + lane], a4 = q.qr[ne + lane];
+        q.qx[lane] = a0;   // ne = 32 > rest here: the slots read and written differ
+        q.qy[lane] = a1;
+        q.qz[lane] = a2;
+        q.qm[lane] = a3;
+        q.qr[lane] = a4;
+    }
+    __syncwarp();
+    q.own >>= ne;
+    q.n = rest;
+}
+
 template <int kSplit>
 __device__ __forceinline__ void sum_buffer_learned(const float *Af, const float *Bf, int nbuf, int h, const float4 xi,
-                                                   float eps2, float rcut2, float c_v, const MlpLane &L, Kahan3 &k)
+                                                   bool live, float eps2, float rcut2, float c_v, const MlpLane &L,
+                                                   LearnedQueue &q, Kahan3 &k)
 {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int nstep = nbuf / kSplit;
-    for (int j0 = 0; j0 < nstep; j0 += 16) {
-        const int j1 = j0 + 16 < nstep ? j0 + 16 : nstep;
-        float px = 0.f, py = 0.f, pz = 0.f;
-        for (int jj = j0; jj < j1; jj++) {
-            const int j = jj * kSplit + h;
-            const int m = j >> 1, sl = j & 1;
-            const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
-            const float mj = Bf[m * 4 + 2 + sl];
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float x = r2 + eps2;
-            const float y = rsqrt_sfu(x);
-            const float y2 = y * y;
-            const float y3 = y2 * y;
-            const float inv3 = fmaf(y3, fmaf(x * -1.5f, y2, 1.5f), y3);
-            const float t = sqrt_sfu(r2 * c_v) - 1.f;
-            const float gh = mlp_warp_eval(t, L);
-            float w = (mj * gh) * inv3;
-            w = r2 < rcut2 ? w : 0.f;
-            px = fmaf(w, dx, px);
-            py = fmaf(w, dy, py);
-            pz = fmaf(w, dz, pz);
+    float px = 0.f, py = 0.f, pz = 0.f;
+    for (int jj = 0; jj < nstep; jj++) {
+        const int j = jj * kSplit + h;
+        const int m = j >> 1, sl = j & 1;
+        const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
+        const float mj = Bf[m * 4 + 2 + sl];
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        // (lanes without a target, massless padding and r = 0 contribute nothing)
+        const bool use = live && r2 < rcut2 && r2 > 0.f && mj != 0.f;
+        const unsigned bal = __ballot_sync(0xffffffffu, use);
+        if (use) {
+            const int slot = q.n + __popc(bal & lt);
+            q.qx[slot] = dx;
+            q.qy[slot] = dy;
+            q.qz[slot] = dz;
+            q.qm[slot] = mj;
+            q.qr[slot] = r2;
+            q.own |= 1ull << slot;
         }
-        k.add(px, py, pz);
+        q.n += __popc(bal);
+        if (q.n >= 32) {
+            learned_flush(q, 32, lane, eps2, c_v, L, px, py, pz);
+            k.add(px, py, pz);
+            px = py = pz = 0.f;
+        }
     }
 }
 
@@ -364,6 +430,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
     __shared__ float4 sB[kPPWarps][kJBuf / 2];
+    __shared__ float sQ[kLearned ? kPPWarps : 1][kLearned ? 5 * kLQ : 1];   // learned: the pair queue
     extern __shared__ float2 sTab[];   // kTable: the factor table (dynamic shared memory)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -405,6 +472,15 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         const f2_t xi = pk(xi4.x, xi4.x), yi = pk(xi4.y, xi4.y), zi = pk(xi4.z, xi4.z);
         Kahan3 k;
         int nbuf = 0;
+        LearnedQueue lq;
+        if (kLearned) {
+            float *qb = sQ[kLearned ? w : 0];
+            lq.qx = qb;
+            lq.qy = qb + kLQ;
+            lq.qz = qb + 2 * kLQ;
+            lq.qm = qb + 3 * kLQ;
+            lq.qr = qb + 4 * kLQ;
+        }
         const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
         // Entries are taken 32 at a time; each round loads 32 concatenated
         // source particles of the batch, one per lane.
@@ -432,7 +508,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                     const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
                     __syncwarp();
                     if (kLearned)
-                        sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+                        sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
                     else if (kTable)
                         sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab,
                                                  pk(a.tab_scale2, a.tab_scale2), k);
@@ -457,13 +533,19 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
         __syncwarp();
         if (kLearned)
-            sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, bx.eps2, bx.rcut2, bx.c_v, L, k);
+            sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
         else if (kTable)
             sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab, pk(a.tab_scale2, a.tab_scale2), k);
         else
             sum_buffer<NPOLY, kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, k);
         inter += (unsigned long long)nbuf * ni;
         staged += nbuf;
+        if (kLearned && lq.n > 0) {
+            // the queue's last, partial batch
+            float px = 0.f, py = 0.f, pz = 0.f;
+            learned_flush(lq, lq.n, lane, bx.eps2, bx.c_v, L, px, py, pz);
+            k.add(px, py, pz);
+        }
         __syncwarp();
         // the kSplit source slots of a target add up their compensated totals
         float tx = k.sx - k.cx, ty = k.sy - k.cy, tz = k.sz - k.cz;
