@@ -249,10 +249,12 @@ def _table_extra(B, ps, lv, pr, stream, t_exact_pp, flush):
             "force_p99_rel_err_exact": p99(acc_e.cpu().numpy()), "oracle_targets": int(tg.size)}
 
 
-def _tree_extra(B, stream, flush, theta=0.3):
-    """The tree part (leaf monopoles at opening angle theta) on the clustered
-    256^3 NFW mixture: whole-step time against theta = 0 and the force error
-    of both against the plain FP64 oracle on sampled targets."""
+def _tree_extra(B, stream, flush, peak, theta=0.3):
+    """The 256^3 NFW mixture (16.8M particles, the largest single-GPU
+    configuration): the plain short-range step (theta = 0) with its PP kernel
+    timed alone, its FP32 roofline and within-R_cut fraction, and the tree
+    part (leaf monopoles at opening angle theta) beside it; force errors of
+    both against the plain FP64 oracle on sampled targets."""
     import torch
     from oracle import force
     from paper_1802_09824_gb300 import synth
@@ -265,7 +267,21 @@ def _tree_extra(B, stream, flush, theta=0.3):
     ref = force.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, targets=tg)
     am = np.linalg.norm(ref.acc, axis=1)
     tau = 1e-3 * np.median(am)
-    out = {"workload": "nfw_mix_256", "n": ps.n, "theta": theta, "leaf_max": 32, "key": "hilbert"}
+    out = {"workload": "nfw_mix_256", "n": ps.n, "theta": theta, "leaf_max": 32, "key": "hilbert", "group_size": 32,
+           "kernel_shape": 0}
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
     for th in (0.0, theta):
         prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, 1, 32, 1, 0, th)
         acc = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
@@ -274,22 +290,27 @@ def _tree_extra(B, stream, flush, theta=0.3):
         g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.25, stream=stream)
         B.ph_graph_launch(g, stream)
         torch.cuda.synchronize()
-        ts = []
-        for _ in range(3):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            B.ph_graph_launch(g, stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
+        t_step = timed(lambda: B.ph_graph_launch(g, stream))
         B.ph_status(pr)
         inter, staged = B.ph_pp_counters(pr)
         a = acc.cpu().numpy()[tg].astype(np.float64)
         e = np.linalg.norm(a - ref.acc, axis=1) / np.maximum(am, tau)
         key = "theta0" if th == 0 else "theta"
-        out[key] = {"step_ms": float(np.median(ts)), "pairs_evaluated": inter,
-                    "force_p99_rel_err": float(np.percentile(e, 99)), "force_max_rel_err": float(e.max())}
+        row = {"step_ms": t_step, "pairs_evaluated": inter,
+               "force_p99_rel_err": float(np.percentile(e, 99)), "force_max_rel_err": float(e.max())}
+        if th == 0:
+            # the PP kernel alone on the same lists, its roofline, and the
+            # useful (r < R_cut) share of the pairs it evaluates
+            t_pp = timed(lambda: B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc, stream))
+            inter, staged = B.ph_pp_counters(pr)
+            n_within = B.ph_count_within(lv, pr, stream)
+            achieved = inter * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12
+            row.update({"pp_ms": t_pp, "build_and_pairs_ms": t_step - t_pp, "interactions_within_rcut": n_within,
+                        "within_fraction": n_within / max(inter, 1),
+                        "value": n_within / (t_step * 1e-3), "unit": UNIT,
+                        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak, "flops_per_interaction": FLOPS_PER_INTERACTION}})
+        out[key] = row
         for h in (g, pr, lv):
             B.ph_free(h)
     out["speedup_vs_theta0"] = out["theta0"]["step_ms"] / out["theta"]["step_ms"]
@@ -373,13 +394,20 @@ def _kdk_extra(B, ps, prm, n_mesh, acc_total, steps=2):
 
 
 def _batched_extra(B, args, dev, stream):
-    """512 boxes: one graph-captured step vs one ph_accel call per box."""
+    """512 boxes: one graph-captured step (the autotuner's leaf size, key,
+    group size and kernel shape for this batch) against the same boxes as
+    512 separately captured per-box steps replayed back to back (per-box
+    launches without host synchronisation), and against one ph_accel call per
+    box (the sizing path: three host synchronisations per box)."""
     import torch
-    from paper_1802_09824_gb300 import synth
+    from paper_1802_09824_gb300 import synth, tuning
     ps = synth.workload("batch_512")
-    prms = [_params(B, bp, args.leaf_max or 32, args.key) for bp in ps.boxes]
+    prms = [_params(B, bp, 32, 1) for bp in ps.boxes]
     pos = torch.from_numpy(ps.pos).to(dev)
     mass = torch.from_numpy(ps.mass).to(dev)
+    t0 = time.perf_counter()
+    prms, tune_info = tuning.tuned(B, pos, mass, ps.offsets, prms, reps=2)
+    tune_s = time.perf_counter() - t0
     acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
     lv = B.ph_build_leaves_batched(pos, mass, ps.offsets, prms, stream)
     pr = B.ph_leaf_pairs(lv, stream)
@@ -398,9 +426,30 @@ def _batched_extra(B, args, dev, stream):
     torch.cuda.synchronize()
     B.ph_status(pr)
     t_graph = e0.elapsed_time(e1) / reps
-    # the same boxes one call each (handles reused per box)
-    handles = [(None, None)] * len(ps.boxes)
+    # the same boxes, each its own captured step (same knobs), replayed one
+    # after another on the stream
     views = [(pos[ps.box_slice(b)], mass[ps.box_slice(b)], acc[ps.box_slice(b)]) for b in range(len(ps.boxes))]
+    per = []
+    for b, (p_, m_, a_) in enumerate(views):
+        l_ = B.ph_build_leaves(p_, m_, prms[b], stream)
+        r_ = B.ph_leaf_pairs(l_, stream)
+        per.append((B.ph_graph_create(l_, r_, p_, m_, B.PH_G_EXACT, None, a_, 0.25, stream), r_, l_))
+    for _ in range(2):
+        for gb, _, _ in per:
+            B.ph_graph_launch(gb, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        for gb, _, _ in per:
+            B.ph_graph_launch(gb, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graphs = e0.elapsed_time(e1) / 3
+    for hs in per:
+        for h in hs:
+            B.ph_free(h)
+    # one ph_accel call per box (handles reused per box)
+    handles = [(None, None)] * len(ps.boxes)
 
     def per_box():
         for b, (p_, m_, a_) in enumerate(views):
@@ -420,9 +469,14 @@ def _batched_extra(B, args, dev, stream):
     B.ph_free(g)
     B.ph_free(pr)
     B.ph_free(lv)
+    p0 = prms[0]
     return {"workload": "batch_512", "n": ps.n, "boxes": len(ps.boxes), "interactions_within_rcut": n_within,
+            "tuned": {"leaf_max": p0.leaf_max, "level_bits": p0.level_bits, "pp_variant": p0.pp_variant,
+                      "group_size": p0.group_size or 32, "key_kind": p0.key_kind, "cache": tune_info["cache"],
+                      "tune_s": tune_s},
             "graph_ms_per_step": t_graph, "graph_kernels_per_step": kernels,
-            "per_box_calls_ms_per_step": t_box, "speedup_graph_vs_per_box": t_box / t_graph,
+            "per_box_graphs_ms_per_step": t_graphs, "speedup_graph_vs_per_box_graphs": t_graphs / t_graph,
+            "per_box_calls_ms_per_step": t_box, "speedup_graph_vs_per_box_calls": t_box / t_graph,
             "value_graph": n_within / (t_graph * 1e-3), "unit": UNIT}
 
 
@@ -652,7 +706,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
         line["table"] = _table_extra(B, ps, lv, pr, stream, t_pp, flush)
-        line["tree"] = _tree_extra(B, stream, flush)
+        line["tree"] = _tree_extra(B, stream, flush, peak)
         n_mesh = int(round(bp.L / (bp.rs / 1.25)))       # R_s = 1.25 mesh cells
         line["pm"] = _pm_extra(B, ps, pos, mass, prm, graph, acc, stream, flush, n_mesh)
         line["kdk"] = _kdk_extra(B, ps, prm, n_mesh, acc)

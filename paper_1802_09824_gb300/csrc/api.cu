@@ -242,6 +242,8 @@ static void fp_mix(uint64_t &h, uint64_t v)
     }
 }
 
+// (The factor table is left out: it has one fixed size, so once made it
+// never moves; the other buffers move when a build needs them larger.)
 uint64_t buffers_fingerprint(const ph_leaves *h, const ph_pairs *p)
 {
     uint64_t f = 1469598103934665603ull;
@@ -249,7 +251,7 @@ uint64_t buffers_fingerprint(const ph_leaves *h, const ph_pairs *p)
                           &h->mass_sorted, &h->cell_first, &h->leaf_flag, &h->group_flag, &h->leaf_scan,
                           &h->group_scan, &h->leaf_first, &h->group_first, &h->leaf_ref, &h->leaf_c4, &h->leaf_h4,
                           &h->group_ref, &h->group_c4, &h->group_h4, &h->leaf_r4, &h->group_r4, &h->box_ext,
-                          &h->work, &h->table, &h->group_cell, &h->group_box, &h->pos_leaf, &h->pos_group,
+                          &h->work, &h->group_cell, &h->group_box, &h->pos_leaf, &h->pos_group,
                           &h->cell_leaf_first, &h->counts, &h->status, &h->temp, &h->group_act, &h->group_act_scan,
                           &h->active_list};
     for (const DevBuf *b : lb) {
