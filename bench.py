@@ -21,9 +21,13 @@ cpu_baseline / --impl reference = the FP64 oracle on the host's cores over a
             bounded sample of the same workload (all sources, a subset of
             targets), in the same unit.
 
-With N > 1 (torchrun) each rank runs an independent replica of the workload
-on its own GPU (the path has no exchange step at this size); value is the
-sum over ranks, time the max over ranks.
+With N > 1 (torchrun) the box is cut into N domains along the Peano-Hilbert
+curve of its ground cells (Sec. 4.1): every rank holds a shard, exchanges
+particles and ghosts with the others over NCCL (the packing in the
+library's kernels) and computes its own particles' forces; value is the
+whole box's interactions per second of the slowest rank (strong scaling).
+--replicas runs N independent whole-box replicas instead (weak scaling);
+--partitioned runs the domain path with one rank too.
 """
 from __future__ import annotations
 
@@ -731,6 +735,110 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_partitioned(args, rank, world, local_rank):
+    """The domain decomposition of Sec. 4.1 (strong scaling of one box over
+    the ranks): every rank holds a contiguous shard of the particles; a step
+    is the device exchange (cells and counts on the device, the cut on the
+    host from the summed counts, packing, NCCL all-to-all, unpacking) plus the
+    captured build + pairs + PP of the rank's local set with its own
+    particles active.  value = the whole box's interactions within R_cut per
+    second of the slowest rank's step."""
+    import torch
+    import torch.distributed as dist
+    from paper_1802_09824_gb300 import binding as B
+    from paper_1802_09824_gb300 import domain, synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist.init_process_group("nccl", device_id=dev) if world > 1 else dist.init_process_group(
+        "nccl", init_method="tcp://127.0.0.1:%d" % (29500 + os.getpid() % 1000), rank=0, world_size=1, device_id=dev)
+    ranks = Ranks(dist, dev)
+    ps = synth.workload(args.workload, scale=args.scale or None)
+    bp = ps.boxes[0]
+    prm = _params(B, bp, args.leaf_max or 32, 1, args.pp_variant)
+    sl = slice(rank * ps.n // world, (rank + 1) * ps.n // world)
+    pos = torch.from_numpy(ps.pos[sl]).to(dev)
+    mass = torch.from_numpy(ps.mass[sl]).to(dev)
+    ids = torch.arange(sl.start, sl.stop, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    step = domain.PartitionedStep(prm)
+    for _ in range(max(args.warmup, 3)):
+        step(pos, mass, ids, stream)
+    torch.cuda.synchronize()
+    B.ph_status(step.lv)
+    B.ph_status(step.pr)
+    n_local, n_own = step.n_local, step.n_own
+    clocks = ClockSampler(_gpu_index(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    ranks.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.ph_launch_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(pos, mass, ids, stream)
+        evs[k][1].record(stream)
+    ranks.barrier()
+    torch.cuda.synchronize()
+    launches = B.ph_launch_counter() - launches0
+    B.ph_status(step.pr)
+    t_step = ranks.max(sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps)
+    # end to end: the shard copied in from pinned host memory, the step, the
+    # own particles' accelerations copied out
+    pos_h = torch.from_numpy(ps.pos[sl]).pin_memory()
+    acc_h = torch.empty((n_own, 3), dtype=torch.float32).pin_memory()
+    ranks.barrier()
+    e2e_ms = []
+    for k in range(max(args.steps // 2, 3)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pos.copy_(pos_h, non_blocking=True)
+        _, a_own = step(pos, mass, ids, stream)
+        acc_h[:a_own.shape[0]].copy_(a_own, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    ranks.barrier()
+    clk = clocks.stop()
+    t_e2e = ranks.max(sum(e2e_ms) / len(e2e_ms))
+    # the whole box's interactions within R_cut (counted once, untimed)
+    n_within = 0
+    if rank == 0:
+        wp = torch.from_numpy(ps.pos).to(dev)
+        wm = torch.from_numpy(ps.mass).to(dev)
+        lv = B.ph_build_leaves(wp, wm, prm, stream)
+        pr = B.ph_leaf_pairs(lv, stream)
+        n_within = B.ph_count_within(lv, pr, stream)
+        B.ph_free(pr)
+        B.ph_free(lv)
+        del wp, wm
+    n_within = ranks.sum(n_within)
+    own_total = ranks.sum(n_own)
+    local_max = ranks.max(n_local)
+    step.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": n_within / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload + (f"@{args.scale}" if args.scale else ""), "n": ps.n,
+                       "leaf_max": prm.leaf_max, "key": "hilbert", "group_size": 32,
+                       "l2": "flushed between steps (256 MB write), per-step CUDA events",
+                       "parallelism": f"domains{world} (Sec. 4.1 cut along the Peano-Hilbert curve, ghost cells, "
+                                      "device exchange over NCCL)"},
+            "e2e": {"value": n_within / (t_e2e * 1e-3), "unit": UNIT, "ms_per_step": t_e2e,
+                    "h2d_bytes_per_step": int(ps.n * 12), "d2h_bytes_per_step": int(own_total * 12),
+                    "call": "domain.PartitionedStep from pinned host shards"},
+            "gpu_launches": launches, "clocks": clk,
+            "partition": {"own_particles": own_total, "largest_local_set": local_max},
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -747,12 +855,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-factor and 512-box measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (leaf_max 32)")
+    ap.add_argument("--partitioned", action="store_true",
+                    help="the domain-decomposed step (default with several ranks; with one rank the whole-box step "
+                         "is the default)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several ranks: independent whole-box replicas instead of the domain decomposition")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank)
+    elif args.partitioned or (world > 1 and not args.replicas):
+        run_partitioned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

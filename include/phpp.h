@@ -425,6 +425,42 @@ int ph_domain_partition(const int64_t *cell_count, int32_t nside, int32_t key_ki
  * cell (periodic 26-neighbour of an own cell), 0 not needed. */
 int ph_domain_halo(const int32_t *owner, int32_t nside, int32_t domain, uint8_t *need);
 
+/*
+ * Device side of the exchange (Sec. 4.1) for ranks that keep particles on the
+ * GPU.  The rows sent between ranks are PH_DOMAIN_ROW doubles per particle:
+ * x, y, z (as given), mass, its flag at the destination (1 own, 2 ghost)
+ * and the caller's int64 identifier (its 64 bits).  These calls share one
+ * scratch area inside the library: calls from several host threads or on
+ * several streams must not overlap.
+ */
+#define PH_DOMAIN_ROW 6
+
+/* ph_domain_cells on the device: d_cell [n] (int32) the ground cell of
+ * every particle, bit for bit the host's decision, and d_counts
+ * [N_side^3] (int64, cleared first) the particles per cell.  Device
+ * buffers.  Synchronises once (PH_ERR_NONFINITE for a non-finite
+ * position). */
+int ph_domain_cells_device(const void *d_pos, int pos_type, int64_t n, const ph_params *params, int32_t *nside,
+                           int32_t *d_cell, int64_t *d_counts, void *stream);
+
+/* The send buffer: for every rank r = 0 .. n_ranks-1 in turn, the rows of
+ * the particles r needs (those in cells r owns, flag 1, and in r's ghost
+ * cells, flag 2; h_owner from ph_domain_partition), in particle order.
+ * d_mass NULL: mass 0 is sent; d_ids NULL: the row index is sent.
+ * h_send_counts [n_ranks] receives the rows per rank even when the capacity
+ * (rows of d_send) is too small, which returns PH_ERR_CAPACITY.
+ * Synchronises once. */
+int ph_domain_pack(const void *d_pos, int pos_type, const float *d_mass, const int64_t *d_ids, const int32_t *d_cell,
+                   int64_t n, const int32_t *h_owner, int32_t nside, int32_t n_ranks, double *d_send,
+                   int64_t send_capacity, int64_t *h_send_counts, void *stream);
+
+/* A rank's local set from the n_recv rows it received: own rows first, then
+ * the ghosts, each in received order; positions written as pos_type,
+ * masses float32, identifiers int64 (device buffers of n_recv).  *h_n_own:
+ * the number of own rows.  Synchronises once. */
+int ph_domain_unpack(const double *d_recv, int64_t n_recv, int pos_type, void *d_pos, float *d_mass, int64_t *d_ids,
+                     int64_t *h_n_own, void *stream);
+
 /* Free any handle (ph_leaves, ph_pairs, ph_mlp, ph_graph, ph_pm, ph_sim).  NULL is a no-op. */
 void ph_free(void *handle);
 
@@ -479,6 +515,18 @@ int ph_pairs_get_view(const ph_pairs *pairs, ph_pairs_view *out);
  * `handle` is the pairs handle of that call, or its leaves handle after a
  * direct-mode call (pairs = NULL). */
 int ph_pp_counters(const void *handle, int64_t *interactions, int64_t *staged);
+
+/* Active-particle mode (Sec. 3.4: only the particles whose step ends need
+ * a force; Sec. 4.1: only a domain's own particles, not its ghosts): with
+ * d_active set (device uint8 [n] in the caller's order of the particles of
+ * the next builds, nonzero = active), every later build of this handle
+ * marks the target groups holding an active particle and the pair builder
+ * gives entries to those groups only, so the PP kernel sums nothing for
+ * the others and writes zero accelerations for them.  The flags are read at
+ * each build: keep the buffer alive and sized for the build's particles.
+ * NULL turns the mode off.  Rebuild the leaves (and the pairs) after
+ * changing it. */
+int ph_leaves_set_active(ph_leaves *leaves, const uint8_t *d_active, int64_t n);
 
 /* Number of ordered pairs (i, j), j != i, with r_ij < rcut in the lists,
  * decided in FP32 exactly as ph_pp_accel decides its cutoff: the work the

@@ -146,6 +146,13 @@ _SIGS = {
                          _VP], ctypes.c_int),
     "ph_domain_partition": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "ph_domain_halo": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
+    "ph_leaves_set_active": ([_VP, _VP, ctypes.c_int64], ctypes.c_int),
+    "ph_domain_cells_device": ([_VP, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ph_params),
+                                ctypes.POINTER(ctypes.c_int32), _VP, _VP, _VP], ctypes.c_int),
+    "ph_domain_pack": ([_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_int32, _VP,
+                        ctypes.c_int64, _VP, _VP], ctypes.c_int),
+    "ph_domain_unpack": ([_VP, ctypes.c_int64, ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int64), _VP],
+                         ctypes.c_int),
     "ph_autotune": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(ph_params),
                      ctypes.c_int32, _VP, ctypes.POINTER(ph_tune_result)], ctypes.c_int),
 }
@@ -524,6 +531,72 @@ def ph_domain_halo(owner, nside, domain):
     need = np.zeros(o.size, np.uint8)
     _check(lib().ph_domain_halo(_ptr(o), int(nside), int(domain), _ptr(need)))
     return need
+
+
+PH_DOMAIN_ROW = 6
+
+
+def ph_leaves_set_active(leaves, active=None):
+    """Active-particle mode: ``active`` a device uint8 tensor [n] (nonzero =
+    active) read at every later build of ``leaves``; None turns it off."""
+    if active is None:
+        _check(lib().ph_leaves_set_active(leaves.ptr, None, 0))
+        leaves._active = None
+        return
+    assert active.dtype == __import__("torch").uint8 and active.is_cuda
+    _check(lib().ph_leaves_set_active(leaves.ptr, _ptr(active), int(active.numel())))
+    leaves._active = active        # kept alive with the handle
+
+
+def ph_domain_cells_device(pos, params, stream=None):
+    """(N_side, cell int32 [n], counts int64 [N_side^3]) on the device."""
+    import torch
+    n = int(pos.shape[0])
+    cells = torch.empty(max(n, 1), dtype=torch.int32, device=pos.device)
+    g = 0
+    while g < 7 and params.L / 2.0 ** (g + 1) >= params.rcut:
+        g += 1
+    counts = torch.empty(8 ** g, dtype=torch.int64, device=pos.device)
+    ns = ctypes.c_int32(0)
+    _check(lib().ph_domain_cells_device(_ptr(pos), _pos_type(pos), n, ctypes.byref(params), ctypes.byref(ns),
+                                        _ptr(cells), _ptr(counts), _stream(stream)))
+    assert ns.value ** 3 == counts.numel()
+    return ns.value, cells[:n], counts
+
+
+def ph_domain_pack(pos, mass, ids, cells, owner, nside, n_ranks, send=None, stream=None):
+    """Rows for every destination rank (device float64 [rows, PH_DOMAIN_ROW]),
+    grouped by rank; returns (send buffer, rows per rank).  The buffer is
+    grown (and the packing repeated) when it is too small."""
+    import torch
+    n = int(pos.shape[0])
+    own = np.ascontiguousarray(np.asarray(owner, np.int32))
+    counts = np.zeros(int(n_ranks), np.int64)
+    if send is None:
+        send = torch.empty((max(2 * n, 1), PH_DOMAIN_ROW), dtype=torch.float64, device=pos.device)
+    rc = lib().ph_domain_pack(_ptr(pos), _pos_type(pos), _ptr(mass), _ptr(ids), _ptr(cells), n, _ptr(own), int(nside),
+                              int(n_ranks), _ptr(send), int(send.shape[0]), _ptr(counts), _stream(stream))
+    if rc == PH_ERR_CAPACITY:
+        send = torch.empty((int(counts.sum()) + 1024, PH_DOMAIN_ROW), dtype=torch.float64, device=pos.device)
+        rc = lib().ph_domain_pack(_ptr(pos), _pos_type(pos), _ptr(mass), _ptr(ids), _ptr(cells), n, _ptr(own),
+                                  int(nside), int(n_ranks), _ptr(send), int(send.shape[0]), _ptr(counts),
+                                  _stream(stream))
+    _check(rc)
+    return send, [int(c) for c in counts]
+
+
+def ph_domain_unpack(recv, n_recv, pos_dtype, stream=None):
+    """(pos [n_recv,3] of pos_dtype, mass float32, ids int64, n_own) of a local
+    set from n_recv received rows (own particles first)."""
+    import torch
+    dev = recv.device
+    pos = torch.empty((max(n_recv, 1), 3), dtype=pos_dtype, device=dev)
+    mass = torch.empty(max(n_recv, 1), dtype=torch.float32, device=dev)
+    ids = torch.empty(max(n_recv, 1), dtype=torch.int64, device=dev)
+    n_own = ctypes.c_int64(0)
+    _check(lib().ph_domain_unpack(_ptr(recv), int(n_recv), _pos_type(pos), _ptr(pos), _ptr(mass), _ptr(ids),
+                                  ctypes.byref(n_own), _stream(stream)))
+    return pos[:n_recv], mass[:n_recv], ids[:n_recv], n_own.value
 
 
 def ph_launch_counter():

@@ -397,6 +397,11 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     size_t tb = sort_temp_bytes(n);
     size_t ts = scan_temp_bytes(n);
     ENS(h->temp, tb > ts ? tb : ts);
+    if (h->active) {
+        ENS(h->group_act, 4 * (N + 1));
+        ENS(h->group_act_scan, 4 * (N + 1));
+        ENS(h->active_list, 4 * N);
+    }
 #undef ENS
     if (rc) {
         if (fresh) {
@@ -760,7 +765,7 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
                         "read count");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "count sync");
     if (rc) return rc;
-    *n_within = (int64_t)v - leaves->n;   // minus the self pairs
+    *n_within = (int64_t)v;
     pr->last_stream = s;
     return PH_OK;
 }
@@ -768,6 +773,28 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
 int64_t ph_launch_counter(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 void ph_debug_fail_allocation(int64_t k) { g_fail_after.store(k < 0 ? -1 : (long long)k); }
+
+int ph_leaves_set_active(ph_leaves *leaves, const uint8_t *d_active, int64_t n)
+{
+    if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
+    if (!d_active) {
+        leaves->active = nullptr;
+        return PH_OK;
+    }
+    if (n < 0 || !is_device_ptr(d_active)) return fail(PH_ERR_ARG, "active flags must be device memory, n >= 0");
+    // the group flags, their scan and the list, for builds of up to n particles
+    // (a build of more particles grows them)
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    int rc = ensure(leaves->group_act, 4 * (N + 1));
+    if (!rc) rc = ensure(leaves->group_act_scan, 4 * (N + 1));
+    if (!rc) rc = ensure(leaves->active_list, 4 * N);
+    if (rc) {
+        leaves->active = nullptr;
+        return rc;
+    }
+    leaves->active = d_active;
+    return PH_OK;
+}
 
 int ph_pp_counters(const void *handle, int64_t *interactions, int64_t *staged)
 {

@@ -793,9 +793,10 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp_walk(PPArgs a)
     }
 }
 
-// Number of (i, j) pairs with r^2 < rcut^2 in the lists, self pairs
-// included (each target meets itself once, at d = 0): the work the cutoff
-// keeps, counted with the PP kernel's own FP32 decision.
+// Number of (i, j) pairs, j != i, with r^2 < rcut^2 in the lists (the self
+// pair is recognised by its index: sources and targets share the sorted
+// order): the work the cutoff keeps, counted with the PP kernel's own FP32
+// decision.  Groups without a list (active-particle mode) count nothing.
 __global__ void __launch_bounds__(kPPThreads) k_count_within(PPArgs a)
 {
     __shared__ float4 sbuf[kPPWarps][kJBuf];
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(kPPThreads) k_count_within(PPArgs a)
                     const float4 pj = buf[jj];
                     const float dx = pj.x - xi.x, dy = pj.y - xi.y, dz = pj.z - xi.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (lane < ni && r2 < rcut2) cnt_within++;
+                    if (lane < ni && r2 < rcut2 && jb + jj != i0 + lane) cnt_within++;   // not the self pair
                 }
             }
         }
