@@ -12,6 +12,7 @@
 // the caller's int64 identifier (its bits).  Within a destination the rows
 // keep the sender's particle order; the local set keeps the received order,
 // own rows first: the exchange is deterministic.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -44,11 +45,22 @@ __device__ __forceinline__ int cell_coord_dev(double xw, double invL, int g, int
     return c < 0 ? 0 : (c >= nside ? nside - 1 : c);
 }
 
-template <int kPosType>
+// Cell counts: with at most kSmemCells cells each block counts into shared
+// memory and adds its counts to the global ones at the end (few global
+// atomics instead of one per particle on a few thousand addresses).
+constexpr int kSmemCells = 4096;
+
+template <int kPosType, bool kSmem>
 __global__ void k_domain_cells(const void *pos, int64_t n, double L, float L_up, double invL, int g,
                                int32_t *cell, unsigned long long *count, uint32_t *status)
 {
+    __shared__ unsigned int s_count[kSmem ? kSmemCells : 1];
     const int nside = 1 << g;
+    const int cells = nside * nside * nside;
+    if (kSmem) {
+        for (int c = threadIdx.x; c < cells; c += blockDim.x) s_count[c] = 0;
+        __syncthreads();
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int c[3];
         bool bad = false;
@@ -69,7 +81,15 @@ __global__ void k_domain_cells(const void *pos, int64_t n, double L, float L_up,
         if (bad) atomicOr(status, ST_NONFINITE);
         const int id = (c[0] * nside + c[1]) * nside + c[2];
         cell[i] = id;
-        atomicAdd(count + id, 1ull);
+        if (kSmem)
+            atomicAdd(s_count + id, 1u);
+        else
+            atomicAdd(count + id, 1ull);
+    }
+    if (kSmem) {
+        __syncthreads();
+        for (int c = threadIdx.x; c < cells; c += blockDim.x)
+            if (s_count[c]) atomicAdd(count + c, (unsigned long long)s_count[c]);
     }
 }
 
@@ -203,12 +223,16 @@ int ph_domain_cells_device(const void *d_pos, int pos_type, int64_t n, const ph_
     uint32_t *st = static_cast<uint32_t *>(g_scratch.status.p);
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(d_counts);
     if (n > 0) {
+        // a grid of at most 2 blocks per SM when the counts go through shared memory
+        const bool smem = cells <= (size_t)kSmemCells;
+        const int grid = smem ? std::min(grid_of(n), 2 * sm_count()) : grid_of(n);
+        const float Lu = float_at_or_above(L);
         if (pos_type == PH_F32)
-            k_domain_cells<PH_F32><<<grid_of(n), kDomThreads, 0, s>>>(d_pos, n, L, float_at_or_above(L), 1.0 / L, g,
-                                                                      d_cell, cnt, st);
+            smem ? k_domain_cells<PH_F32, true><<<grid, kDomThreads, 0, s>>>(d_pos, n, L, Lu, 1.0 / L, g, d_cell, cnt, st)
+                 : k_domain_cells<PH_F32, false><<<grid, kDomThreads, 0, s>>>(d_pos, n, L, Lu, 1.0 / L, g, d_cell, cnt, st);
         else
-            k_domain_cells<PH_F64><<<grid_of(n), kDomThreads, 0, s>>>(d_pos, n, L, float_at_or_above(L), 1.0 / L, g,
-                                                                      d_cell, cnt, st);
+            smem ? k_domain_cells<PH_F64, true><<<grid, kDomThreads, 0, s>>>(d_pos, n, L, Lu, 1.0 / L, g, d_cell, cnt, st)
+                 : k_domain_cells<PH_F64, false><<<grid, kDomThreads, 0, s>>>(d_pos, n, L, Lu, 1.0 / L, g, d_cell, cnt, st);
         count_launch();
         rc = cuda_check(cudaGetLastError(), "cells kernel");
     }
