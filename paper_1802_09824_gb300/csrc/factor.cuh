@@ -123,7 +123,8 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // weights and biases that produce z and -ln2 into the weights that consume
 // the activation (see mlp_lane_load), so a unit costs an SFU ex2, an add, an
 // SFU reciprocal and a multiply.  (A Newton reciprocal on the FMA pipe for
-// part of the units, to unload the SFU, measured slower.)
+// part of the units, to unload the SFU, measured slower, and so did one
+// reciprocal for several units by batch inversion.)
 __device__ __forceinline__ float silu_scaled(float z)
 {
     return z * rcp_sfu(1.f + ex2_sfu(z));
@@ -136,22 +137,53 @@ __device__ __forceinline__ f2_t silu_scaled2(f2_t z)
     return mul2(z, pk(rcp_sfu(lo_of(den)), rcp_sfu(hi_of(den))));
 }
 
-// Round to BF16 (ties away from zero) with integer operations: the BF16 value
-// in the upper half of an FP32 word.  Keeps the conversion off the SFU pipe.
-__device__ __forceinline__ uint32_t bf16_round_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
+// The same split for a packed pair, as two BF16x2 registers (first value in
+// the low half): hi = bf16(x), lo = bf16(x - hi), both rounded to nearest.
+__device__ __forceinline__ void split_pack2(f2_t x, uint32_t &hi, uint32_t &lo)
+{
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(hi_of(x)), "f"(lo_of(x)));
+    const f2_t hf = pk(__uint_as_float(hi << 16), __uint_as_float(hi & 0xFFFF0000u));
+    const f2_t l = sub2(x, hf);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(hi_of(l)), "f"(lo_of(l)));
+}
 
-// Two BF16 values (upper halves of a and b) into one register, a in the low
-// half.
-__device__ __forceinline__ uint32_t pack_upper(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+// Layer 1 as a table.  Its input is the one scalar t = 2r/rcut - 1 in
+// [-1, 1], so each of its 16 activations h(t) = silu(w1 t + b1) is a smooth
+// function of t alone: the kernels tabulate them (in FP32, through
+// silu_scaled) at kL1Nodes equally spaced nodes t_i = i D - 1,
+// D = 2/(kL1Nodes - 1), and interpolate linearly.  The interpolation error of
+// a unit is at most (D^2/8) max|h''| = (D^2/8) w1^2 / 2 (|silu''| <= 1/2 at
+// 0), 1.4e-5 for |w1| = 3.8 (the trained 128^3 network), which moves g_hat by
+// ~1e-6, below what the BF16 hi/lo split of layer 2's operands does (~7e-6);
+// each network's validation measures g_hat through this table.  Node i holds,
+// for each lane quad q, the units {2q, 2q+1, 2q+8, 2q+9} of the A fragment
+// (one float4): the table has kL1Nodes x 4 float4 (32 KB).
+constexpr int kL1Nodes = 512;
+
+// Fill the table (all threads of the block; the caller synchronises).
+// w: network parameters in the flat order of kMlpParams.
+__device__ __forceinline__ void l1_table_fill(const float *w, float4 *tab)
+{
+    const float kz = -1.4426950408889634f;   // -log2(e)
+    const float D = 2.f / (float)(kL1Nodes - 1);
+    for (int e = threadIdx.x; e < 4 * kL1Nodes; e += blockDim.x) {
+        const int i = e >> 2, q = e & 3;
+        const float t = fmaf((float)i, D, -1.f);
+        float v[4];
+        const int cols[4] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9};
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[c] = silu_scaled(fmaf(kz * w[cols[c]], t, kz * w[16 + cols[c]]));
+        tab[e] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
 
 // Per-lane share of the network for warp-level evaluation with
 // mma.sync.m16n8k16 (BF16 in, FP32 accumulate).  Lane = 4 g + q: the lane
 // owns rows g and g+8 of each 16-pair tile and hidden columns
 // {2q, 2q+1, 2q+8, 2q+9}; the 16x16 second layer is two n8 halves.
 // Weights are stored in the scaled units of silu_scaled: W1, b1 and b2
-// times -log2(e), W3 times -ln2 (W2 and b3 unchanged).
+// times -log2(e), W3 times -ln2 (W2 and b3 unchanged); layer 1 is the table.
 struct MlpLane {
-    f2_t w1[4], b1[4];           // layer 1 for the lane's 4 columns (each duplicated: rows g, g + 8)
     uint32_t bhi[2][2], blo[2][2];   // W2^T fragments (hi / lo parts), per n-half
     float b2[2][2];              // bias of output columns 8h + 2q, 8h + 2q + 1
     f2_t w3[2];                  // W3 of the same two columns, per n-half
@@ -164,11 +196,6 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
     const float ka = -0.6931471805599453f;   // -ln(2)
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     const int cols[4] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9};
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        L.w1[c] = pk(kz * w[cols[c]], kz * w[cols[c]]);
-        L.b1[c] = pk(kz * w[16 + cols[c]], kz * w[16 + cols[c]]);
-    }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int n = g + 8 * h;             // output unit of this B column
@@ -187,50 +214,54 @@ __device__ __forceinline__ void mlp_lane_load(const float *w, MlpLane &L)
     L.b3 = w[320];
 }
 
-// Split two activations into BF16 hi and lo parts packed for the A fragment.
-__device__ __forceinline__ void split_pack(float x0, float x1, uint32_t &hi, uint32_t &lo)
-{
-    const uint32_t h0 = bf16_round_bits(x0), h1 = bf16_round_bits(x1);
-    const float l0 = x0 - __uint_as_float(h0), l1 = x1 - __uint_as_float(h1);
-    hi = pack_upper(h0, h1);
-    lo = pack_upper(bf16_round_bits(l0), bf16_round_bits(l1));
-}
-
 // The network's factor for the warp's 32 pairs: lane i passes the input
-// z0 = 2r/rcut - 1 of its pair and receives g_hat of its pair.  Layer 1 and
-// both SiLU layers in FP32 on the FMA/SFU pipes, two units per packed
-// instruction (the lane's rows g and g + 8 share layer 1's weights; its two
-// columns 2q, 2q + 1 of a row share layer 3's accumulator pair); layer 2 as
-// BF16 tensor-core MMAs with FP32 accumulation, activations and weights split
-// into BF16 hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16 bits.
-__device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L)
+// z0 = 2r/rcut - 1 of its pair and receives g_hat of its pair.  Layer 1 from
+// the table (linear interpolation, two units per packed instruction), layer
+// 2 as BF16 tensor-core MMAs with FP32 accumulation, activations and weights
+// split into BF16 hi + lo parts (hi*hi + lo*hi + hi*lo), which keeps ~16
+// bits, then its SiLUs and layer 3 in FP32 (the lane's two columns 2q, 2q + 1
+// of a row share layer 3's accumulator pair).
+__device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L, const float4 *tab)
 {
     const int lane = threadIdx.x & 31;
-    const int g = lane >> 2;
+    const int g = lane >> 2, q = lane & 3;
+    const float kInv = 0.5f * (float)(kL1Nodes - 1);   // 1 / D
+    const float kMagic = 12582912.f;                   // 1.5 * 2^23: adding it rounds to an integer
     float out = 0.f;
 #pragma unroll
     for (int tile = 0; tile < 2; tile++) {
         const float za = __shfl_sync(0xffffffffu, z0, 16 * tile + g);
         const float zb = __shfl_sync(0xffffffffu, z0, 16 * tile + g + 8);
-        const f2_t zab = pk(za, zb);
-        f2_t h[4];   // column c of rows (g, g + 8)
-#pragma unroll
-        for (int c = 0; c < 4; c++) h[c] = silu_scaled2(fma2(L.w1[c], zab, L.b1[c]));
+        // node index i = floor(u) (clamped into the table) and fraction u - i of rows g, g + 8
+        const f2_t u0 = fma2(pk(za, zb), pk(kInv, kInv), pk(kInv, kInv));
+        const f2_t u = pk(fminf(fmaxf(lo_of(u0), 0.f), (float)(kL1Nodes - 1)),
+                          fminf(fmaxf(hi_of(u0), 0.f), (float)(kL1Nodes - 1)));
+        const f2_t y = add2(add2(u, pk(-0.5f, -0.5f)), pk(kMagic, kMagic));
+        const f2_t fr = sub2(u, sub2(y, pk(kMagic, kMagic)));
+        const int ia = __float_as_int(lo_of(y)) - __float_as_int(kMagic);
+        const int ib = __float_as_int(hi_of(y)) - __float_as_int(kMagic);
+        const float4 a0 = tab[4 * ia + q], a1 = tab[4 * ia + 4 + q];
+        const float4 b0 = tab[4 * ib + q], b1 = tab[4 * ib + 4 + q];
+        const f2_t fa = pk(lo_of(fr), lo_of(fr)), fb = pk(hi_of(fr), hi_of(fr));
+        const f2_t va0 = pk(a0.x, a0.y), va1 = pk(a0.z, a0.w), vb0 = pk(b0.x, b0.y), vb1 = pk(b0.z, b0.w);
         uint32_t Ahi[4], Alo[4];
-        split_pack(lo_of(h[0]), lo_of(h[1]), Ahi[0], Alo[0]);   // row g, cols 2q, 2q+1
-        split_pack(hi_of(h[0]), hi_of(h[1]), Ahi[1], Alo[1]);   // row g+8
-        split_pack(lo_of(h[2]), lo_of(h[3]), Ahi[2], Alo[2]);   // row g, cols 2q+8, 2q+9
-        split_pack(hi_of(h[2]), hi_of(h[3]), Ahi[3], Alo[3]);   // row g+8
-        f2_t ya = 0ull, yb = 0ull;   // rows g and g + 8: (even column, odd column) partial sums
+        split_pack2(fma2(fa, sub2(pk(a1.x, a1.y), va0), va0), Ahi[0], Alo[0]);   // row g, cols 2q, 2q+1
+        split_pack2(fma2(fb, sub2(pk(b1.x, b1.y), vb0), vb0), Ahi[1], Alo[1]);   // row g+8
+        split_pack2(fma2(fa, sub2(pk(a1.z, a1.w), va1), va1), Ahi[2], Alo[2]);   // row g, cols 2q+8, 2q+9
+        split_pack2(fma2(fb, sub2(pk(b1.z, b1.w), vb1), vb1), Ahi[3], Alo[3]);   // row g+8
+        f2_t s[4];   // per n-half hh: s[2 hh] row g, s[2 hh + 1] row g + 8 (columns 8hh + 2q, + 1)
 #pragma unroll
         for (int hh = 0; hh < 2; hh++) {
             float d[4] = {L.b2[hh][0], L.b2[hh][1], L.b2[hh][0], L.b2[hh][1]};
             mma_bf16(d, Alo, L.bhi[hh][0], L.bhi[hh][1]);
             mma_bf16(d, Ahi, L.blo[hh][0], L.blo[hh][1]);
             mma_bf16(d, Ahi, L.bhi[hh][0], L.bhi[hh][1]);
-            ya = fma2(L.w3[hh], silu_scaled2(pk(d[0], d[1])), ya);
-            yb = fma2(L.w3[hh], silu_scaled2(pk(d[2], d[3])), yb);
+            s[2 * hh] = silu_scaled2(pk(d[0], d[1]));
+            s[2 * hh + 1] = silu_scaled2(pk(d[2], d[3]));
         }
+        // rows g and g + 8: (even column, odd column) partial sums
+        const f2_t ya = fma2(L.w3[1], s[2], mul2(L.w3[0], s[0]));
+        const f2_t yb = fma2(L.w3[1], s[3], mul2(L.w3[0], s[1]));
         float sa = lo_of(ya) + hi_of(ya), sb = lo_of(yb) + hi_of(yb);
         sa += __shfl_xor_sync(0xffffffffu, sa, 1);
         sa += __shfl_xor_sync(0xffffffffu, sa, 2);

@@ -231,7 +231,10 @@ __global__ void k_adam(AdamArgs a)
 __global__ void k_validate(const float *theta, FactorConsts fc, int n_grid, unsigned int *max_err_bits)
 {
     __shared__ float w[kMlpParams];
+    __shared__ float4 tab[4 * kL1Nodes];
     for (int e = threadIdx.x; e < kMlpParams; e += blockDim.x) w[e] = theta[e];
+    __syncthreads();
+    l1_table_fill(w, tab);
     __syncthreads();
     MlpLane L;
     mlp_lane_load(w, L);
@@ -242,7 +245,7 @@ __global__ void k_validate(const float *theta, FactorConsts fc, int n_grid, unsi
         const float x = (float)min(k, n_grid - 1) / (float)n_grid;
         const float t = 2.f * x - 1.f;
         const float r = x * fc.rcut;
-        const float gh = mlp_warp_eval(t, L);
+        const float gh = mlp_warp_eval(t, L, tab);
         const float g = exact_factor(r * r, t, fc.poly, fc.npoly, fc.c_e);
         const float err = fabsf(gh / g - 1.f);
         if (k < n_grid) worst = fmaxf(worst, isfinite(err) ? err : 3.0e38f);

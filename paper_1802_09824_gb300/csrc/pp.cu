@@ -232,105 +232,118 @@ __device__ __forceinline__ void sum_buffer_table(const float4 *A, const float4 *
 // Learned factor.  The network is evaluated warp-wide (32 pairs per call on
 // the tensor cores), and only pairs within R_cut need it: each lane takes
 // its next source each step, and the pairs with 0 < r^2 < R_cut^2 are
-// appended (ballot order) to a per-warp queue of their separation, mass and
-// r^2; whenever the queue holds 32 pairs, lane k evaluates queue entry k
-// (softened inverse cube, network, weight) and writes the entry's force back
-// into its slot, and every lane adds the forces of the entries it owns in
-// slot order (a deterministic order), then the remaining entries move to the
-// front.  Pairs beyond R_cut, the self pair and coincident pairs contribute
-// exactly zero and are not queued.
-constexpr int kLQ = 64;   // queue slots per warp (at most 31 pending + 32 new)
+// appended (ballot order) to a per-warp ring of 64 slots holding their
+// separation and mass; whenever 32 pairs are pending, lane k evaluates the
+// k-th oldest (softened inverse cube, network, weight) and writes the
+// entry's force back into its slot, and every lane adds the forces of the
+// entries it owns in slot order (a deterministic order).  The evaluated half
+// of the ring is then free and the pending entries stay where they are.
+// Pairs beyond R_cut, the self pair and coincident pairs contribute exactly
+// zero and are not queued.
+constexpr int kLQ = 64;   // ring slots per warp (at most 31 pending + 32 new)
 struct LearnedQueue {
-    float *qx, *qy, *qz, *qm, *qr;   // per-warp slots in shared memory
-    int n = 0;                       // queued entries (warp-uniform)
-    unsigned long long own = 0;      // slots this lane's entries occupy
+    float4 *q;                       // per-warp ring in shared memory: (dx, dy, dz, m_j);
+                                     // slot kLQ holds zeros
+    const float4 *l1;                // layer 1's table (shared memory)
+    int head = 0;                    // slot of the oldest pending entry: 0 or 32 (warp-uniform)
+    int n = 0;                       // pending entries (warp-uniform)
+    unsigned long long own = 0;      // ring slots this lane's entries occupy
 };
 
-// Evaluate the first `ne` (<= 32) queue entries and add their forces to their
-// owners' run sums.
+// Evaluate the `ne` (<= 32) oldest entries and add their forces to their
+// owners' sums (px, py, pz).
 __device__ __forceinline__ void learned_flush(LearnedQueue &q, int ne, int lane, float eps2, float c_v,
                                               const MlpLane &L, float &px, float &py, float &pz)
 {
     __syncwarp();
     const bool on = lane < ne;
-    const float dx = on ? q.qx[lane] : 0.f, dy = on ? q.qy[lane] : 0.f, dz = on ? q.qz[lane] : 0.f;
-    const float mj = on ? q.qm[lane] : 0.f, r2 = on ? q.qr[lane] : 0.f;
-    const float x = r2 + eps2;
-    const float y = rsqrt_sfu(x);
-    const float y2 = y * y;
-    const float y3 = y2 * y;
-    const float inv3 = fmaf(y3, fmaf(x * -1.5f, y2, 1.5f), y3);
+    float4 *win = q.q + q.head;      // the 32 slots being evaluated
+    const float4 e = on ? win[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float r2 = fmaf(e.z, e.z, fmaf(e.y, e.y, e.x * e.x));   // as when it was queued
+    const float y = rsqrt_sfu(r2 + eps2);
+    const float inv3 = y * y * y;
     const float t = sqrt_sfu(r2 * c_v) - 1.f;
-    const float gh = mlp_warp_eval(t, L);
-    const float w = on ? (mj * gh) * inv3 : 0.f;
+    const float gh = mlp_warp_eval(t, L, q.l1);
+    const float w = on ? (e.w * gh) * inv3 : 0.f;
+    win[lane] = make_float4(w * e.x, w * e.y, w * e.z, 0.f);   // the slot this lane read
     __syncwarp();
-    q.qx[lane] = w * dx;
-    q.qy[lane] = w * dy;
-    q.qz[lane] = w * dz;
-    __syncwarp();
-    unsigned m32 = (unsigned)q.own & (ne == 32 ? 0xffffffffu : ((1u << ne) - 1u));
+    // the lane's entries in slot order, two loads in flight (a missing second
+    // one reads the zero slot)
+    unsigned m32 = (unsigned)(q.own >> q.head) & (ne == 32 ? 0xffffffffu : ((1u << ne) - 1u));
     while (m32) {
-        const int b = __ffs(m32) - 1;
+        const int b0 = q.head + __ffs(m32) - 1;
         m32 &= m32 - 1u;
-        px += q.qx[b];
-        py += q.qy[b];
-        pz += q.qz[b];
+        const int b1 = m32 ? q.head + __ffs(m32) - 1 : kLQ;
+        m32 &= m32 - 1u;
+        const float4 f0 = q.q[b0], f1 = q.q[b1];
+        px += f0.x;
+        py += f0.y;
+        pz += f0.z;
+        px += f1.x;
+        py += f1.y;
+        pz += f1.z;
     }
     __syncwarp();
-    // the entries behind the evaluated ones move to the front
-    const int rest = q.n - ne;
-    if (lane < rest) {
-        const float a0 = q.qx[ne + lane], a1 = q.qy[ne + lane], a2 = q.qz[ne + lane];
-        const float a3 = q.qm[ne + lane], a4 = q.qr[ne + lane];
-        q.qx[lane] = a0;   // ne = 32 > rest here: the slots read and written differ
-        q.qy[lane] = a1;
-        q.qz[lane] = a2;
-        q.qm[lane] = a3;
-        q.qr[lane] = a4;
-    }
-    __syncwarp();
-    q.own >>= ne;
-    q.n = rest;
+    q.own &= q.head ? 0x00000000ffffffffull : 0xffffffff00000000ull;
+    q.head ^= 32;
+    q.n -= ne;
 }
 
+// One step of the learned sum: a source at separation (dx, dy, dz) and r^2
+// from the lane's target; a pair within R_cut joins the queue, and 32
+// pending pairs are evaluated.
+__device__ __forceinline__ void learned_step(float dx, float dy, float dz, float r2, float mj, bool live, unsigned lt,
+                                             int lane, float eps2, float rcut2, float c_v, const MlpLane &L,
+                                             LearnedQueue &q, float &px, float &py, float &pz)
+{
+    // (lanes without a target, massless padding and r = 0 contribute nothing)
+    const bool use = live && r2 < rcut2 && r2 > 0.f && mj != 0.f;
+    const unsigned bal = __ballot_sync(0xffffffffu, use);
+    if (use) {
+        const int slot = (q.head + q.n + __popc(bal & lt)) & (kLQ - 1);
+        q.q[slot] = make_float4(dx, dy, dz, mj);
+        q.own |= 1ull << slot;
+    }
+    q.n += __popc(bal);
+    if (q.n >= 32) learned_flush(q, 32, lane, eps2, c_v, L, px, py, pz);
+}
+
+// The staged sources against the lane's target; the forces of this buffer
+// are summed plainly and added to the compensated total once.
 template <int kSplit>
-__device__ __forceinline__ void sum_buffer_learned(const float *Af, const float *Bf, int nbuf, int h, const float4 xi,
+__device__ __forceinline__ void sum_buffer_learned(const float4 *A, const float4 *B, int nbuf, int h, const float4 xi,
                                                    bool live, float eps2, float rcut2, float c_v, const MlpLane &L,
                                                    LearnedQueue &q, Kahan3 &k)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int nstep = nbuf / kSplit;
     float px = 0.f, py = 0.f, pz = 0.f;
-    for (int jj = 0; jj < nstep; jj++) {
-        const int j = jj * kSplit + h;
-        const int m = j >> 1, sl = j & 1;
-        const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
-        const float mj = Bf[m * 4 + 2 + sl];
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        // (lanes without a target, massless padding and r = 0 contribute nothing)
-        const bool use = live && r2 < rcut2 && r2 > 0.f && mj != 0.f;
-        const unsigned bal = __ballot_sync(0xffffffffu, use);
-        if (use) {
-            const int slot = q.n + __popc(bal & lt);
-            q.qx[slot] = dx;
-            q.qy[slot] = dy;
-            q.qz[slot] = dz;
-            q.qm[slot] = mj;
-            q.qr[slot] = r2;
-            q.own |= 1ull << slot;
+    if (kSplit == 1) {
+        // both sources of a staged pair per iteration: (x, x', y, y') and (z, z', m, m')
+        const f2_t xi2 = pk(xi.x, xi.x), yi2 = pk(xi.y, xi.y), zi2 = pk(xi.z, xi.z);
+        for (int m = 0; m < nbuf / 2; m++) {
+            const float4 a = A[m], b = B[m];
+            const f2_t dx = sub2(pk(a.x, a.y), xi2), dy = sub2(pk(a.z, a.w), yi2), dz = sub2(pk(b.x, b.y), zi2);
+            const f2_t r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            learned_step(lo_of(dx), lo_of(dy), lo_of(dz), lo_of(r2), b.z, live, lt, lane, eps2, rcut2, c_v, L, q,
+                         px, py, pz);
+            learned_step(hi_of(dx), hi_of(dy), hi_of(dz), hi_of(r2), b.w, live, lt, lane, eps2, rcut2, c_v, L, q,
+                         px, py, pz);
         }
-        q.n += __popc(bal);
-        if (q.n >= 32) {
-            learned_flush(q, 32, lane, eps2, c_v, L, px, py, pz);
-            k.add(px, py, pz);
-            px = py = pz = 0.f;
+    } else {
+        const float *Af = reinterpret_cast<const float *>(A), *Bf = reinterpret_cast<const float *>(B);
+        const int nstep = nbuf / kSplit;
+        for (int jj = 0; jj < nstep; jj++) {
+            const int j = jj * kSplit + h;
+            const int m = j >> 1, sl = j & 1;
+            const float dx = Af[m * 4 + sl] - xi.x, dy = Af[m * 4 + 2 + sl] - xi.y, dz = Bf[m * 4 + sl] - xi.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            learned_step(dx, dy, dz, r2, Bf[m * 4 + 2 + sl], live, lt, lane, eps2, rcut2, c_v, L, q, px, py, pz);
         }
     }
+    k.add(px, py, pz);
 }
 
-// Pad the staged sources with massless ones (at the group's reference point)
-// to a multiple of 2 kSplit; returns the padded count.
 template <int kSplit>
 __device__ __forceinline__ int pad_sources(float *Af, float *Bf, int nbuf, int lane)
 {
@@ -430,8 +443,9 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
 {
     __shared__ float4 sA[kPPWarps][kJBuf / 2];
     __shared__ float4 sB[kPPWarps][kJBuf / 2];
-    __shared__ float sQ[kLearned ? kPPWarps : 1][kLearned ? 5 * kLQ : 1];   // learned: the pair queue
-    extern __shared__ float2 sTab[];   // kTable: the factor table (dynamic shared memory)
+    __shared__ float4 sQ[kLearned ? kPPWarps : 1][kLearned ? kLQ + 1 : 1];   // learned: the pair queue
+    extern __shared__ float4 sDyn[];   // dynamic: the factor table (kTable) or layer 1's table (kLearned)
+    float2 *const sTab = reinterpret_cast<float2 *>(sDyn);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     float4 *A = sA[w], *Bq = sB[w];
@@ -439,7 +453,11 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
     const int ng = *a.n_groups;
     unsigned long long inter = 0, staged = 0;
     MlpLane L;
-    if (kLearned) mlp_lane_load(a.mlp_w, L);
+    if (kLearned) {
+        mlp_lane_load(a.mlp_w, L);
+        l1_table_fill(a.mlp_w, sDyn);
+        __syncthreads();
+    }
     if (kTable) {
         for (int i = threadIdx.x; i <= kTabN; i += blockDim.x) sTab[i] = a.table[i];
         __syncthreads();
@@ -474,12 +492,9 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         int nbuf = 0;
         LearnedQueue lq;
         if (kLearned) {
-            float *qb = sQ[kLearned ? w : 0];
-            lq.qx = qb;
-            lq.qy = qb + kLQ;
-            lq.qz = qb + 2 * kLQ;
-            lq.qm = qb + 3 * kLQ;
-            lq.qr = qb + 4 * kLQ;
+            lq.q = sQ[kLearned ? w : 0];
+            lq.l1 = sDyn;
+            if (lane == 0) lq.q[kLQ] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int64_t e1 = a.group_off[g + 1] < a.cap ? a.group_off[g + 1] : a.cap;
         // Entries are taken 32 at a time; each round loads 32 concatenated
@@ -508,7 +523,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                     const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
                     __syncwarp();
                     if (kLearned)
-                        sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
+                        sum_buffer_learned<kSplit>(A, Bq, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
                     else if (kTable)
                         sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab,
                                                  pk(a.tab_scale2, a.tab_scale2), k);
@@ -533,7 +548,7 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
         const int padded = pad_sources<kSplit>(Af, Bf, nbuf, lane);
         __syncwarp();
         if (kLearned)
-            sum_buffer_learned<kSplit>(Af, Bf, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
+            sum_buffer_learned<kSplit>(A, Bq, padded, hs, xi4, ti < ni, bx.eps2, bx.rcut2, bx.c_v, L, lq, k);
         else if (kTable)
             sum_buffer_table<kSplit>(A, Bq, padded >> 1, hs, xi, yi, zi, c, sTab, pk(a.tab_scale2, a.tab_scale2), k);
         else
@@ -957,9 +972,21 @@ int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
     const int grid = sm_count() * kBlocks0;
-    if (lv->group_size == 8) k_pp<10, true, kBlocks0, 4, false><<<grid, kPPThreads, 0, s>>>(a);
-    else if (lv->group_size == 16) k_pp<10, true, kBlocks0, 2, false><<<grid, kPPThreads, 0, s>>>(a);
-    else k_pp<10, true, kBlocks0, 1, false><<<grid, kPPThreads, 0, s>>>(a);
+    constexpr int kL1Bytes = 4 * kL1Nodes * (int)sizeof(float4);
+    static bool attr = false;   // the opt-in above 48 KB of shared memory, once per process
+    if (!attr) {
+        rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 4, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+        if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 2, false>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+        if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 1, false>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+        if (rc) return rc;
+        attr = true;
+    }
+    if (lv->group_size == 8) k_pp<10, true, kBlocks0, 4, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
+    else if (lv->group_size == 16) k_pp<10, true, kBlocks0, 2, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
+    else k_pp<10, true, kBlocks0, 1, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
     count_launch();
     return cuda_check(cudaGetLastError(), "learned pp kernel");
 }
