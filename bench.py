@@ -253,6 +253,47 @@ def _table_extra(B, ps, lv, pr, stream, t_exact_pp, flush):
             "force_p99_rel_err_exact": p99(acc_e.cpu().numpy()), "oracle_targets": int(tg.size)}
 
 
+def _group16_extra(B, ps, pos, mass, stream, flush, peak, n_within):
+    """16-particle target groups (two lanes per target, leaf 16, kernel shape
+    1) on the same particles: fewer pairs beyond R_cut, against the whole
+    step's cost.  The autotuner measures this among its candidates; here it is
+    reported beside the headline configuration."""
+    import torch
+    bp = ps.boxes[0]
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 16, B.PH_KEY_HILBERT, 16, 1, 1)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device="cuda")
+    lv = B.ph_build_leaves(pos, mass, prm, stream)
+    pr = B.ph_leaf_pairs(lv, stream)
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc, stream)
+    torch.cuda.synchronize()
+    inter, _ = B.ph_pp_counters(pr)
+    graph = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.25, stream=stream)
+    B.ph_graph_launch(graph, stream)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=8):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_step = timed(lambda: B.ph_graph_launch(graph, stream))
+    t_pp = timed(lambda: B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc, stream))
+    for h in (graph, pr, lv):
+        B.ph_free(h)
+    return {"config": "leaf 16, 16-particle groups (2 lanes per target), kernel shape 1, same particles",
+            "step_ms": t_step, "pp_ms": t_pp, "interactions_evaluated": inter, "within_fraction": n_within / max(inter, 1),
+            "frac_evaluated": inter * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12 / peak,
+            "frac_within_rcut": n_within * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12 / peak,
+            "value": n_within / (t_step * 1e-3)}
+
+
 def _tree_extra(B, stream, flush, peak, theta=0.3):
     """The 256^3 NFW mixture (16.8M particles, the largest single-GPU
     configuration): the plain short-range step (theta = 0) with its PP kernel
@@ -711,6 +752,7 @@ def run_ours(args, rank, world, local_rank):
         line["learned"] = _learned_extra(B, ps, lv, pr, stream, t_pp)
         line["table"] = _table_extra(B, ps, lv, pr, stream, t_pp, flush)
         line["tree"] = _tree_extra(B, stream, flush, peak)
+        line["group16"] = _group16_extra(B, ps, pos, mass, stream, flush, peak, n_within)
         n_mesh = int(round(bp.L / (bp.rs / 1.25)))       # R_s = 1.25 mesh cells
         line["pm"] = _pm_extra(B, ps, pos, mass, prm, graph, acc, stream, flush, n_mesh)
         line["kdk"] = _kdk_extra(B, ps, prm, n_mesh, acc)
