@@ -24,6 +24,8 @@
 
 namespace phpp {
 
+int pp_learned_setup();   // the learned PP kernels' shared-memory opt-in (pp.cu)
+
 void fit_factor_poly(double U, int deg, float *coef);
 
 namespace {
@@ -306,6 +308,8 @@ int new_mlp(double rs, double rcut, float tol, ph_mlp **out)
         return fail(PH_ERR_ARG, "rs and rcut must be finite and > 0");
     const double U = rcut / (2.0 * rs);
     if (U > 4.6) return fail(PH_ERR_ARG, "rcut/rs = %g above the supported 9.2", rcut / rs);
+    int rc0 = pp_learned_setup();
+    if (rc0) return rc0;
     ph_mlp *h = new (std::nothrow) ph_mlp();
     if (!h) return fail(PH_ERR_OOM, "host allocation failed");
     h->rs = rs;

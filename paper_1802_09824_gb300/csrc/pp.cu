@@ -964,6 +964,25 @@ static void launch_table_one(int grid, cudaStream_t s, const PPArgs &a)
     k_pp<10, false, kBlocks0, kSplit, true, true><<<grid, kPPThreads, kTabBytes, s>>>(a);
 }
 
+constexpr int kL1Bytes = 4 * kL1Nodes * (int)sizeof(float4);   // layer 1's table (dynamic shared memory)
+
+// The learned kernels' opt-in above 48 KB of shared memory, once per
+// process; called when a network handle is made, so that it never runs
+// inside a stream capture.
+int pp_learned_setup()
+{
+    static bool done = false;
+    if (done) return PH_OK;
+    int rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 4, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+    if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 2, false>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+    if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 1, false>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
+    if (!rc) done = true;
+    return rc;
+}
+
 int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_w, float *d_acc, cudaStream_t s)
 {
     PPArgs a;
@@ -972,18 +991,8 @@ int pp_learned_device(const ph_leaves *lv, const ph_pairs *pr, const float *mlp_
     int rc = cuda_check(cudaMemsetAsync(pr->work.p, 0, 24, s), "reset work queue");
     if (rc) return rc;
     const int grid = sm_count() * kBlocks0;
-    constexpr int kL1Bytes = 4 * kL1Nodes * (int)sizeof(float4);
-    static bool attr = false;   // the opt-in above 48 KB of shared memory, once per process
-    if (!attr) {
-        rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 4, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
-        if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 2, false>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
-        if (!rc) rc = cuda_check(cudaFuncSetAttribute(k_pp<10, true, kBlocks0, 1, false>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kL1Bytes), "smem opt-in");
-        if (rc) return rc;
-        attr = true;
-    }
+    rc = pp_learned_setup();
+    if (rc) return rc;
     if (lv->group_size == 8) k_pp<10, true, kBlocks0, 4, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
     else if (lv->group_size == 16) k_pp<10, true, kBlocks0, 2, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
     else k_pp<10, true, kBlocks0, 1, false><<<grid, kPPThreads, kL1Bytes, s>>>(a);
