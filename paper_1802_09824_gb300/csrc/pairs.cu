@@ -63,7 +63,8 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
 {
-    __shared__ int2 s_run[kThreads / 32][32];   // per warp: (lane, first leaf - excl) of each run
+    __shared__ int2 s_run[kThreads / 32][32];   // per warp: (image code, first leaf - excl) of each run
+    __shared__ float4 s_sh[kThreads / 32][32];  // per warp: the run's cell offset (dx h, dy h, dz h) in the group's frame
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
         const float rf2 = bx.rfilt2;
         // this lane's neighbour cell
         const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
-        int l0 = 0, cnt = 0;
+        int l0 = 0, cnt = 0, img = 13;
         if (lane < 27) {
             const int ax = gx + dx, ay = gy + dy, az = gz + dz;
             const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                 l0 = a.cell_leaf_first[nc];
                 cnt = a.cell_leaf_first[nc + 1] - l0;
             }
+            img = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
         }
         const int incl = warp_incl_scan_i(cnt, lane);
         const int excl = incl - cnt;
@@ -107,7 +109,11 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
         // the lanes with leaves, in lane order, as runs (lane, first leaf - excl):
         // candidate q of run k is leaf (first - excl) + q
         const unsigned nonempty = __ballot_sync(0xffffffffu, cnt > 0);
-        if (cnt > 0) s_run[w][__popc(nonempty & lt)] = make_int2(lane, l0 - excl);
+        if (cnt > 0) {
+            const int rk = __popc(nonempty & lt);
+            s_run[w][rk] = make_int2(img, l0 - excl);
+            s_sh[w][rk] = make_float4((lane / 9 - 1) * hc, ((lane / 3) % 3 - 1) * hc, (lane % 3 - 1) * hc, 0.f);
+        }
         __syncwarp();
         int64_t count = 0;
         int before = 0;   // runs started before q0
@@ -118,18 +124,18 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             const int r = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;   // owner run
             before += __popc(starts);
             const int2 ru = s_run[w][r];
-            const int o = ru.x, lb = ru.y;
+            const int im = ru.x, lb = ru.y;
+            const float4 sh = s_sh[w][r];
             bool acc = false, mono = false;
             int l = 0;
-            const int odx = o / 9 - 1, ody = (o / 3) % 3 - 1, odz = o % 3 - 1;
             float4 lc = make_float4(0.f, 0.f, 0.f, 0.f), lh = lc;   // w: first particle, particles (bits)
             if (q < total) {
                 l = lb + q;
                 lc = a.leaf_c4[l];
                 lh = a.leaf_h4[l];
-                const float px = fmaxf(fabsf((lc.x + odx * hc) - gc.x) - (gh.x + lh.x), 0.f);
-                const float py = fmaxf(fabsf((lc.y + ody * hc) - gc.y) - (gh.y + lh.y), 0.f);
-                const float pz = fmaxf(fabsf((lc.z + odz * hc) - gc.z) - (gh.z + lh.z), 0.f);
+                const float px = fmaxf(fabsf((lc.x + sh.x) - gc.x) - (gh.x + lh.x), 0.f);
+                const float py = fmaxf(fabsf((lc.y + sh.y) - gc.y) - (gh.y + lh.y), 0.f);
+                const float pz = fmaxf(fabsf((lc.z + sh.z) - gc.z) - (gh.z + lh.z), 0.f);
                 acc = px * px + py * py + pz * pz < rf2;
                 // tree part (Sec. 3.3): accepted as one mass-centre particle
                 // when both opening angles are below theta, theta_1 = (A + B)/R
@@ -137,9 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
                 // the leaf's, R the distance of the box centres), i.e. R >
                 // (A + B)/theta and R > A + B/theta, compared as squares
                 if (acc && bx.c_acc < INFINITY) {
-                    const float ex = (lc.x + odx * hc) - gc.x;
-                    const float ey = (lc.y + ody * hc) - gc.y;
-                    const float ez = (lc.z + odz * hc) - gc.z;
+                    const float ex = (lc.x + sh.x) - gc.x;
+                    const float ey = (lc.y + sh.y) - gc.y;
+                    const float ez = (lc.z + sh.z) - gc.z;
                     const float R2 = ex * ex + ey * ey + ez * ez;
                     const float A = 2.f * fmaxf(fmaxf(gh.x, gh.y), gh.z);
                     const float Bw = 2.f * fmaxf(fmaxf(lh.x, lh.y), lh.z);
@@ -152,10 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             if (kFill && acc) {
                 const int64_t pos = base + count + __popc(bal & lt);
                 if (pos < a.cap) {
-                    const int ax = gx + odx, ay = gy + ody, az = gz + odz;
-                    const int sx = ax < 0 ? -1 : (ax >= ns ? 1 : 0);
-                    const int sy = ay < 0 ? -1 : (ay >= ns ? 1 : 0);
-                    const int sz = az < 0 ? -1 : (az >= ns ? 1 : 0);
+                    const int sx = im / 9 - 1, sy = (im / 3) % 3 - 1, sz = im % 3 - 1;   // periodic image
                     float4 e;
                     if ((sx | sy | sz) == 0) {
                         // the rounded difference of two FP32 numbers, exactly the
