@@ -475,6 +475,7 @@ extern "C" {
 int ph_build_leaves(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params,
                     void *stream, ph_leaves **leaves)
 {
+    TraceRange trace_("ph_build_leaves");
     if (n < 0) return fail(PH_ERR_ARG, "n must be >= 0");
     int64_t off[2] = {0, n};
     return leaves_common(pos, pos_type, mass, off, 1, params, stream, leaves);
@@ -483,6 +484,7 @@ int ph_build_leaves(const void *pos, int pos_type, const float *mass, int64_t n,
 int ph_build_leaves_batched(const void *pos, int pos_type, const float *mass, const int64_t *box_offsets,
                             int32_t n_boxes, const ph_params *params, void *stream, ph_leaves **leaves)
 {
+    TraceRange trace_("ph_build_leaves_batched");
     if (!box_offsets) return fail(PH_ERR_ARG, "box_offsets must not be NULL");
     return leaves_common(pos, pos_type, mass, box_offsets, n_boxes, params, stream, leaves);
 }
@@ -516,6 +518,7 @@ int ph_pairs_reserve(ph_pairs **pairs, int64_t capacity)
 
 int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
 {
+    TraceRange trace_("ph_leaf_pairs");
     if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
     if (!pairs) return fail(PH_ERR_ARG, "pairs must not be NULL");
     ph_pairs *p = *pairs;
@@ -563,6 +566,7 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
 int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, const ph_mlp *mlp, float *acc,
                 void *stream)
 {
+    TraceRange trace_("ph_pp_accel");
     if (!leaves || leaves->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "leaves is not a ph_leaves handle");
     if (pairs && pairs->kind != KIND_PAIRS) return fail(PH_ERR_STATE, "pairs is not a ph_pairs handle");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
@@ -629,6 +633,7 @@ int ph_pp_accel(const ph_leaves *leaves, const ph_pairs *pairs, int g_mode, cons
 int ph_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params, int g_mode,
              const ph_mlp *mlp, float *acc, void *stream, ph_leaves **leaves, ph_pairs **pairs)
 {
+    TraceRange trace_("ph_accel");
     if (!leaves) return fail(PH_ERR_ARG, "leaves must not be NULL");
     int rc = ph_build_leaves(pos, pos_type, mass, n, params, stream, leaves);
     if (rc) return rc;
@@ -747,6 +752,7 @@ int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
 
 int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_within, void *stream)
 {
+    TraceRange trace_("ph_count_within");
     if (!leaves || leaves->kind != KIND_LEAVES || !pairs || pairs->kind != KIND_PAIRS || !n_within)
         return fail(PH_ERR_ARG, "bad arguments");
     if (pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");

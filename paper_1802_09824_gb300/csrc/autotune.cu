@@ -19,6 +19,7 @@ extern "C" {
 int ph_autotune(const void *d_pos, int pos_type, const float *d_mass, const int64_t *box_offsets, int32_t n_boxes,
                 const ph_params *params, int32_t reps, void *stream, ph_tune_result *out)
 {
+    TraceRange trace_("ph_autotune");
     if (!d_pos || !box_offsets || !params || !out || n_boxes < 1 || reps < 1 || reps > 50)
         return fail(PH_ERR_ARG, "ph_autotune: bad arguments");
     if (!is_device_ptr(d_pos) || (d_mass && !is_device_ptr(d_mass)))

@@ -203,6 +203,7 @@ extern "C" {
 int ph_domain_cells_device(const void *d_pos, int pos_type, int64_t n, const ph_params *params, int32_t *nside,
                            int32_t *d_cell, int64_t *d_counts, void *stream)
 {
+    TraceRange trace_("ph_domain_cells_device");
     if (!params || !nside || !d_counts || (n > 0 && (!d_pos || !d_cell))) return fail(PH_ERR_ARG, "NULL argument");
     if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
     if (n < 0) return fail(PH_ERR_ARG, "n must be >= 0");
@@ -248,6 +249,7 @@ int ph_domain_pack(const void *d_pos, int pos_type, const float *d_mass, const i
                    int64_t n, const int32_t *h_owner, int32_t nside, int32_t n_ranks, double *d_send,
                    int64_t send_capacity, int64_t *h_send_counts, void *stream)
 {
+    TraceRange trace_("ph_domain_pack");
     if (!h_owner || !h_send_counts || (n > 0 && (!d_pos || !d_cell))) return fail(PH_ERR_ARG, "NULL argument");
     if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
     if (n < 0 || n >= ((int64_t)1 << 31) || send_capacity < 0) return fail(PH_ERR_ARG, "bad n or capacity");
@@ -330,6 +332,7 @@ int ph_domain_pack(const void *d_pos, int pos_type, const float *d_mass, const i
 int ph_domain_unpack(const double *d_recv, int64_t n_recv, int pos_type, void *d_pos, float *d_mass, int64_t *d_ids,
                      int64_t *h_n_own, void *stream)
 {
+    TraceRange trace_("ph_domain_unpack");
     if (!h_n_own || (n_recv > 0 && (!d_recv || !d_pos || !d_mass || !d_ids))) return fail(PH_ERR_ARG, "NULL argument");
     if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
     if (n_recv < 0 || n_recv >= ((int64_t)1 << 31)) return fail(PH_ERR_ARG, "bad n_recv");

@@ -55,6 +55,7 @@ extern "C" {
 int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int pos_type, const float *d_mass,
                     int g_mode, const ph_mlp *mlp, float *d_acc, double headroom, void *stream, ph_graph **out)
 {
+    TraceRange trace_("ph_graph_create");
     if (!leaves || leaves->kind != KIND_LEAVES || (pairs && pairs->kind != KIND_PAIRS) || !out)
         return fail(PH_ERR_ARG, "ph_graph_create: leaves and out must be valid, pairs valid or NULL");
     if (pairs && pairs->built_from != leaves) return fail(PH_ERR_STATE, "pairs were not built from these leaves");
@@ -144,6 +145,7 @@ int ph_graph_create(ph_leaves *leaves, ph_pairs *pairs, const void *d_pos, int p
 
 int ph_graph_launch(ph_graph *g, void *stream)
 {
+    TraceRange trace_("ph_graph_launch");
     if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
     // the capture holds the handles' buffer addresses: a rebuild that moved
     // or dropped any of them (larger n, a failed build) ends the graph's use
@@ -157,6 +159,7 @@ int ph_graph_launch(ph_graph *g, void *stream)
 
 int ph_graph_launch_host(ph_graph *g, const void *h_pos, const float *h_mass, float *h_acc, void *stream)
 {
+    TraceRange trace_("ph_graph_launch_host");
     if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
     if (g->n > 0 && (!h_pos || !h_acc)) return fail(PH_ERR_ARG, "h_pos and h_acc must not be NULL");
     if (h_mass && !g->d_mass) return fail(PH_ERR_ARG, "the graph was captured without masses");

@@ -382,6 +382,7 @@ extern "C" {
 int ph_sim_create(const double *pos, const double *mom, const float *mass, int64_t n, const ph_params *params,
                   const ph_kdk_params *kp, double t0, void *stream, ph_sim **sim)
 {
+    TraceRange trace_("ph_sim_create");
     if (!sim || !params || !kp || !pos || !mom) return fail(PH_ERR_ARG, "sim, params, kp, pos and mom must not be NULL");
     if (*sim) return fail(PH_ERR_STATE, "*sim must be NULL (a new simulation)");
     if (n < 1 || n >= (int64_t)1 << 31) return fail(PH_ERR_ARG, "n must be 1..2^31-1");
@@ -441,6 +442,7 @@ int ph_sim_create(const double *pos, const double *mom, const float *mass, int64
 
 int ph_sim_step(ph_sim *sim, int32_t n_steps, void *stream)
 {
+    TraceRange trace_("ph_sim_step");
     if (!sim || sim->kind != KIND_SIM || n_steps < 0) return fail(PH_ERR_ARG, "bad arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     sim->last_stream = s;

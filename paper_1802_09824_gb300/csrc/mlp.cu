@@ -380,6 +380,7 @@ extern "C" {
 
 int ph_mlp_create(const float *weights, double rs, double rcut, float tol, void *stream, ph_mlp **mlp)
 {
+    TraceRange trace_("ph_mlp_create");
     if (!weights || !mlp) return fail(PH_ERR_ARG, "weights and mlp must not be NULL");
     ph_mlp *h = nullptr;
     int rc = new_mlp(rs, rcut, tol, &h);
@@ -400,6 +401,7 @@ int ph_mlp_create(const float *weights, double rs, double rcut, float tol, void 
 int ph_mlp_train(const ph_train_params *tp, double rs, double rcut, const float *init_weights, void *stream,
                  ph_mlp **mlp)
 {
+    TraceRange trace_("ph_mlp_train");
     if (!tp || !mlp) return fail(PH_ERR_ARG, "train params and mlp must not be NULL");
     if (tp->n_samples < 1 || tp->batch < 1 || tp->steps < 0 || !(tp->lr0 > 0) || tp->lr_min < 0)
         return fail(PH_ERR_ARG, "bad training parameters");
@@ -607,6 +609,7 @@ int ph_mlp_load(const char *path, float tol, void *stream, ph_mlp **mlp)
 int ph_mlp_loss_grad(const float *weights, const float *z0, const float *target, int64_t n, float *grad, float *loss,
                      void *stream)
 {
+    TraceRange trace_("ph_mlp_loss_grad");
     if (!weights || !z0 || !target || !grad || n < 1 || n > (1 << 24)) return fail(PH_ERR_ARG, "bad arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DevBuf th, zz, tt, part, st;

@@ -8,9 +8,21 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/phpp.h"
 
 namespace phpp {
+
+// An NVTX range around a public call, for profilers that record ranges (ncu
+// --nvtx, Nsight Systems); without an attached tool it costs a test of a
+// function pointer.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxPoly = 16;          // highest degree of the factor polynomial

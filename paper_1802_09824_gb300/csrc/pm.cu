@@ -383,6 +383,7 @@ extern "C" {
 int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, const ph_params *params,
                 int32_t n_mesh, float *acc, float *pot, int32_t accumulate, void *stream, ph_pm **pm)
 {
+    TraceRange trace_("ph_pm_accel");
     if (!pm || !params) return fail(PH_ERR_ARG, "pm and params must not be NULL");
     if (pos_type != PH_F32 && pos_type != PH_F64) return fail(PH_ERR_ARG, "pos_type must be PH_F32 or PH_F64");
     if (n < 0 || n >= (int64_t)1 << 31) return fail(PH_ERR_ARG, "n must be 0..2^31-1");
