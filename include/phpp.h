@@ -668,6 +668,19 @@ int64_t ph_launch_counter(void);
  */
 void ph_debug_fail_allocation(int64_t k);
 
+/*
+ * Debug bounds checks (a testing aid; no counterpart in the paper).  A
+ * library built with bounds checks (`python -m paper_1802_09824_gb300.build
+ * --checked`: libphpp_checked.so, the same sources compiled with
+ * PHPP_BOUNDS_CHECK) tests the indices of its kernels' buffer accesses; an
+ * index outside its buffer skips the access (no trap, no wait) and is
+ * counted.  This call synchronises the device, returns the number of such
+ * accesses since the last call in *hits and the site of the first one in
+ * *first_site (a small code, 0 = none), and clears both.  Returns
+ * PH_ERR_STATE from a library built without the checks.
+ */
+int ph_debug_bounds(int64_t *hits, int32_t *first_site);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,9 @@ import weakref
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libphpp.so")
+# PHPP_LIB selects another build of the same library (e.g. the bounds-checked
+# libphpp_checked.so); the default is the normal build.
+LIB_PATH = os.environ.get("PHPP_LIB") or os.path.join(_HERE, "libphpp.so")
 
 PH_OK = 0
 PH_WARN_FALLBACK = 1
@@ -129,6 +131,7 @@ _SIGS = {
     "ph_mlp_save": ([_VP, ctypes.c_char_p], ctypes.c_int),
     "ph_mlp_load": ([ctypes.c_char_p, ctypes.c_float, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_debug_fail_allocation": ([ctypes.c_int64], None),
+    "ph_debug_bounds": ([ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "ph_graph_create": ([_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP,
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
@@ -399,6 +402,15 @@ def ph_mlp_load(path, tol=0.0, stream=None):
 def ph_debug_fail_allocation(k):
     """Make the k-th next device allocation of the library fail (k < 0: off)."""
     lib().ph_debug_fail_allocation(int(k))
+
+
+def ph_debug_bounds():
+    """(out-of-bounds accesses skipped since the last call, site of the first)
+    of a library built with bounds checks; raises from a normal build."""
+    h = ctypes.c_int64(0)
+    s = ctypes.c_int32(0)
+    _check(lib().ph_debug_bounds(ctypes.byref(h), ctypes.byref(s)))
+    return h.value, s.value
 
 
 def ph_mlp_loss_grad(weights, z0, target, stream=None):

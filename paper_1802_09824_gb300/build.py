@@ -2,7 +2,10 @@
 
 Each .cu file under csrc/ is compiled in parallel with nvcc into _build/,
 then linked into paper_1802_09824_gb300/libphpp.so.  Objects are rebuilt
-only when a source or header is newer than the object.
+only when a source or header is newer than the object.  `--checked` (or
+build(checked=True)) makes libphpp_checked.so from the same sources with the
+debug bounds checks of csrc/checks.cuh compiled in (objects in
+_build/checked/).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libphpp.so")
+CHECKED_OUT = os.path.join(HERE, "libphpp_checked.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code is compiled without floating-point contraction, so host-side
@@ -35,11 +39,11 @@ def _newest_header() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, checked: bool = False) -> str:
+    obj = os.path.join(BUILD, "checked" if checked else "", os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _newest_header()):
         return obj
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *(["-DPHPP_BOUNDS_CHECK"] if checked else []), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,21 +55,22 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, checked: bool = False) -> str:
+    os.makedirs(os.path.join(BUILD, "checked") if checked else BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if (not os.path.exists(OUT)) or os.path.getmtime(OUT) < max(os.path.getmtime(o) for o in objs):
+        objs = list(ex.map(lambda s: _compile(s, verbose, checked), srcs))
+    out = CHECKED_OUT if checked else OUT
+    if (not os.path.exists(out)) or os.path.getmtime(out) < max(os.path.getmtime(o) for o in objs):
         libdir = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "lib64")
-        cmd = [_nvcc(), *ARCH, "-shared", *objs, "-o", OUT + ".tmp", "-lcudart", "-lcufft",
+        cmd = [_nvcc(), *ARCH, "-shared", *objs, "-o", out + ".tmp", "-lcudart", "-lcufft",
                "-Xlinker", "-rpath", "-Xlinker", libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(OUT + ".tmp", OUT)
-    return OUT
+        os.replace(out + ".tmp", out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -65,6 +65,16 @@ static std::atomic<long long> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// The translation units' bounds-word readers (checked builds), filled by
+// their static initialisers when the library is loaded.
+static std::vector<int (*)(unsigned int *, unsigned int *)> &bounds_readers()
+{
+    static std::vector<int (*)(unsigned int *, unsigned int *)> v;
+    return v;
+}
+
+void register_bounds_reader(int (*read)(unsigned int *hits, unsigned int *site)) { bounds_readers().push_back(read); }
+
 void set_error(const char *fmt, ...)
 {
     va_list ap;
@@ -779,6 +789,26 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
 int64_t ph_launch_counter(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 void ph_debug_fail_allocation(int64_t k) { g_fail_after.store(k < 0 ? -1 : (long long)k); }
+
+int ph_debug_bounds(int64_t *hits, int32_t *first_site)
+{
+    if (!hits || !first_site) return fail(PH_ERR_ARG, "ph_debug_bounds: null output");
+    *hits = 0;
+    *first_site = 0;
+#ifndef PHPP_BOUNDS_CHECK
+    return fail(PH_ERR_STATE, "library built without bounds checks");
+#else
+    int rc = cuda_check(cudaDeviceSynchronize(), "bounds sync");
+    if (rc) return rc;
+    for (auto read : bounds_readers()) {
+        unsigned int h = 0, site = 0;
+        if (read(&h, &site)) return fail(PH_ERR_CUDA, "reading the bounds words failed");
+        *hits += h;
+        if (!*first_site && site) *first_site = (int32_t)site;
+    }
+    return PH_OK;
+#endif
+}
 
 int ph_leaves_set_active(ph_leaves *leaves, const uint8_t *d_active, int64_t n)
 {

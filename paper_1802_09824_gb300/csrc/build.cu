@@ -25,6 +25,7 @@
 #include <climits>
 #include <cmath>
 
+#include "checks.cuh"
 #include "curve.cuh"
 #include "handles.cuh"
 
@@ -123,7 +124,8 @@ __global__ void k_gather(const void *pos, const float *mass, int64_t n, const ui
                          const BoxDev *boxes, int T, double *xw, float *mass_sorted, uint32_t *status)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = perm[k];
+        int64_t i = perm[k];
+        if (!in_bounds(i, n, BS_BUILD_ROW)) i = 0;
         const int bi = 3 * T < 64 ? (int)(keys[k] >> (3 * T)) : 0;
         const BoxDev &bx = boxes[bi];
         double x, y, z;
@@ -243,7 +245,7 @@ __global__ void k_firsts(const int32_t *lflag, const int32_t *lscan, const int32
                          int64_t n, int32_t *lfirst, int32_t *gfirst, long long *lext, long long *gext)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        if (lflag[k]) {
+        if (lflag[k] && in_bounds(lscan[k], n, BS_BUILD_ROW)) {
             const int64_t l = lscan[k];
             lfirst[l] = (int32_t)k;
 #pragma unroll
@@ -252,7 +254,7 @@ __global__ void k_firsts(const int32_t *lflag, const int32_t *lscan, const int32
                 lext[6 * l + 3 + d] = LLONG_MIN;
             }
         }
-        if (gflag[k]) {
+        if (gflag[k] && in_bounds(gscan[k], n, BS_BUILD_ROW)) {
             const int64_t l = gscan[k];
             gfirst[l] = (int32_t)k;
 #pragma unroll
@@ -419,8 +421,10 @@ __global__ void k_pos(int64_t n, const double *xw, const float *mass_sorted, con
                       float4 *pos_leaf, float4 *pos_group)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l = leaf_scan[k + 1] - 1;
-        const int64_t g = group_scan[k + 1] - 1;
+        int64_t l = leaf_scan[k + 1] - 1;
+        int64_t g = group_scan[k + 1] - 1;
+        if (!in_bounds(l, n, BS_BUILD_ROW)) l = 0;
+        if (!in_bounds(g, n, BS_BUILD_ROW)) g = 0;
         const float4 lr4 = leaf_r4[l], gr4 = group_r4[g];
         const float lrf[3] = {lr4.x, lr4.y, lr4.z}, grf[3] = {gr4.x, gr4.y, gr4.z};
         float p[3], q[3];

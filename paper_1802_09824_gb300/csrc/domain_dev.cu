@@ -16,6 +16,7 @@
 #include <cmath>
 #include <vector>
 
+#include "checks.cuh"
 #include "handles.cuh"
 
 using namespace phpp;
@@ -153,6 +154,7 @@ __global__ void k_unpack(const double *recv, int64_t n, const int32_t *own, cons
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         // own rows keep their order at the front, ghosts theirs behind them
         const int64_t o = own[i] ? (int64_t)excl[i] : n_own + (i - (int64_t)excl[i]);
+        if (!in_bounds(o, n, BS_DOM_ROW)) continue;
         const double *r = recv + PH_DOMAIN_ROW * i;
         if (kPosType == PH_F32) {
             float *p = static_cast<float *>(pos) + 3 * o;

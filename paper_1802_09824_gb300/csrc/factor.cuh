@@ -4,6 +4,7 @@
 
 #include <cuda_bf16.h>
 
+#include "checks.cuh"
 #include "phpp_internal.cuh"
 
 namespace phpp {
@@ -238,8 +239,10 @@ __device__ __forceinline__ float mlp_warp_eval(float z0, const MlpLane &L, const
                           fminf(fmaxf(hi_of(u0), 0.f), (float)(kL1Nodes - 1)));
         const f2_t y = add2(add2(u, pk(-0.5f, -0.5f)), pk(kMagic, kMagic));
         const f2_t fr = sub2(u, sub2(y, pk(kMagic, kMagic)));
-        const int ia = __float_as_int(lo_of(y)) - __float_as_int(kMagic);
-        const int ib = __float_as_int(hi_of(y)) - __float_as_int(kMagic);
+        int ia = __float_as_int(lo_of(y)) - __float_as_int(kMagic);
+        int ib = __float_as_int(hi_of(y)) - __float_as_int(kMagic);
+        if (!in_bounds(ia, kL1Nodes - 1, BS_L1_TABLE)) ia = 0;
+        if (!in_bounds(ib, kL1Nodes - 1, BS_L1_TABLE)) ib = 0;
         const float4 a0 = tab[4 * ia + q], a1 = tab[4 * ia + 4 + q];
         const float4 b0 = tab[4 * ib + q], b1 = tab[4 * ib + 4 + q];
         const f2_t fa = pk(lo_of(fr), lo_of(fr)), fb = pk(hi_of(fr), hi_of(fr));

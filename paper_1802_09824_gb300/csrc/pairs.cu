@@ -14,6 +14,7 @@
 // offset of an accepted pair is the difference of the reference points
 // rounded once to FP32: in FP32 directly when no periodic image is involved
 // (the reference points are FP32 numbers), from the FP64 points otherwise.
+#include "checks.cuh"
 #include "handles.cuh"
 
 namespace phpp {
@@ -39,6 +40,7 @@ struct PairArgs {
     int64_t n_particles;     // mass-centre particle of leaf l: pos_leaf[n_particles + l]
     int64_t cap;
     uint32_t *status;
+    int64_t n_leaf_rows;     // rows of the leaf arrays (bounds checks)
 };
 
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
@@ -121,7 +123,8 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             const int q = q0 + lane;
             const unsigned sq = (unsigned)(excl - q0);
             const unsigned starts = __reduce_or_sync(0xffffffffu, (cnt > 0 && sq < 32u) ? 1u << sq : 0u);
-            const int r = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;   // owner run
+            int r = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;   // owner run
+            if (!in_bounds(r, 32, BS_PAIR_RUN)) r = 0;
             before += __popc(starts);
             const int2 ru = s_run[w][r];
             const int im = ru.x, lb = ru.y;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             bool acc = false, mono = false;
             int l = 0;
             float4 lc = make_float4(0.f, 0.f, 0.f, 0.f), lh = lc;   // w: first particle, particles (bits)
-            if (q < total) {
+            if (q < total && in_bounds(lb + q, a.n_leaf_rows, BS_PAIR_LEAF)) {
                 l = lb + q;
                 lc = a.leaf_c4[l];
                 lh = a.leaf_h4[l];
@@ -211,6 +214,7 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     a.cell_leaf_first = static_cast<const int32_t *>(lv->cell_leaf_first.p);
     a.leaf_c4 = static_cast<const float4 *>(lv->leaf_c4.p);
     a.leaf_h4 = static_cast<const float4 *>(lv->leaf_h4.p);
+    a.n_leaf_rows = (int64_t)(lv->leaf_h4.bytes / sizeof(float4));
     a.leaf_ref = static_cast<const double *>(lv->leaf_ref.p);
     a.leaf_r4 = static_cast<const float4 *>(lv->leaf_r4.p);
     a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);

@@ -160,6 +160,10 @@ int cuda_check(cudaError_t e, const char *what);
 // Host-side count of kernel launches issued by the library (all threads).
 void count_launch(int n = 1);
 
+// Debug bounds checks (checks.cuh): each translation unit of a checked build
+// registers a reader of its device words (hits, first site) at load time.
+void register_bounds_reader(int (*read)(unsigned int *hits, unsigned int *site));
+
 // ---------------------------------------------------------------- kernels
 // scan.cu: exclusive scans over n elements (n read from device memory when
 // d_n != nullptr, else the host value).  out[n] receives the total.

@@ -28,6 +28,7 @@
 #include <new>
 #include <vector>
 
+#include "checks.cuh"
 #include "phpp_internal.cuh"
 
 struct ph_pm {
@@ -161,7 +162,8 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     const long long q = __float2ll_rn(wab * wzm[c]);
-                    if (q) atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
+                    if (q && in_bounds(row + jz[c], (int64_t)N * N * N, BS_PM_NODE))
+                        atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
                 }
             }
     }

@@ -82,6 +82,7 @@ struct PPArgs {
     // tabulated factor (PH_G_TABLE): kTabN + 1 nodes (f(r_i), f'(r_i) dr)
     const float2 *table;
     float tab_scale2;                // (kTabN / rcut)^2
+    int64_t n_pos;                   // rows of pos_leaf (bounds checks)
 };
 
 struct Kahan3 {
@@ -190,8 +191,10 @@ __device__ __forceinline__ void interact2_table(const float4 a, const float4 b, 
     const f2_t mg = pk(kMagic, kMagic);
     const f2_t y = add2(u, mg);
     const f2_t fr = sub2(u, sub2(y, mg));                            // r / dr - nearest node
-    const int i0 = min(__float_as_int(lo_of(y)) - 0x4B400000, kTabN);
-    const int i1 = min(__float_as_int(hi_of(y)) - 0x4B400000, kTabN);
+    int i0 = min(__float_as_int(lo_of(y)) - 0x4B400000, kTabN);
+    int i1 = min(__float_as_int(hi_of(y)) - 0x4B400000, kTabN);
+    if (!in_bounds(i0, kTabN + 1, BS_F_TABLE)) i0 = 0;
+    if (!in_bounds(i1, kTabN + 1, BS_F_TABLE)) i1 = 0;
     const float2 t0 = tab[i0], t1 = tab[i1];
     const f2_t f = pk(fmaf(t0.y, lo_of(fr), t0.x), fmaf(t1.y, hi_of(fr), t1.x));
     const f2_t w = mul2(mul2(pk(b.z, b.w), f), inv3);
@@ -299,8 +302,8 @@ __device__ __forceinline__ void learned_step(float dx, float dy, float dz, float
     // (lanes without a target, massless padding and r = 0 contribute nothing)
     const bool use = live && r2 < rcut2 && r2 > 0.f && mj != 0.f;
     const unsigned bal = __ballot_sync(0xffffffffu, use);
-    if (use) {
-        const int slot = (q.head + q.n + __popc(bal & lt)) & (kLQ - 1);
+    const int slot = (q.head + q.n + __popc(bal & lt)) & (kLQ - 1);
+    if (use && in_bounds(slot, kLQ, BS_PP_QUEUE)) {
         q.q[slot] = make_float4(dx, dy, dz, mj);
         q.own |= 1ull << slot;
     }
@@ -423,7 +426,7 @@ struct Round {
         oy = __shfl_sync(0xffffffffu, b.ent.y, o);
         oz = __shfl_sync(0xffffffffu, b.ent.z, o);
         valid = q < b.total;
-        p = valid ? a.pos_leaf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        p = (valid && in_bounds(j, a.n_pos, BS_PP_SOURCE)) ? a.pos_leaf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 };
 
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
                     nbuf = 0;
                     __syncwarp();
                 }
-                if (keep) {
-                    const int idx = nbuf + __popc(bal & lt);
+                const int idx = nbuf + __popc(bal & lt);
+                if (keep && in_bounds(idx, kJBuf, BS_PP_STAGE)) {
                     const int m = idx >> 1, sl = idx & 1;
                     Af[m * 4 + sl] = p.x;
                     Af[m * 4 + 2 + sl] = p.y;
@@ -665,8 +668,8 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp_walk(PPArgs a)
                     nbuf = 0;
                     __syncwarp();
                 }
-                if (keep) {
-                    const int idx = nbuf + __popc(bal & lt);
+                const int idx = nbuf + __popc(bal & lt);
+                if (keep && in_bounds(idx, kJBuf, BS_PP_STAGE)) {
                     const int m = idx >> 1, sl = idx & 1;
                     Af[m * 4 + sl] = p.x;
                     Af[m * 4 + 2 + sl] = p.y;
@@ -885,6 +888,7 @@ static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArg
     a.group_h4 = static_cast<const float4 *>(lv->group_h4.p);
     a.pos_group = static_cast<const float4 *>(lv->pos_group.p);
     a.pos_leaf = static_cast<const float4 *>(lv->pos_leaf.p);
+    a.n_pos = (int64_t)(lv->pos_leaf.bytes / sizeof(float4));
     a.leaf_first = static_cast<const int32_t *>(lv->leaf_first.p);
     a.perm = static_cast<const int32_t *>(lv->keys_in_alt ? lv->vals_alt.p : lv->vals.p);
     a.group_off = pr ? static_cast<const int64_t *>(pr->group_off.p) : nullptr;

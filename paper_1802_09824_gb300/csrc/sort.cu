@@ -8,6 +8,7 @@
 // consecutive positions.
 #include <utility>
 
+#include "checks.cuh"
 #include "phpp_internal.cuh"
 
 namespace phpp {
@@ -119,8 +120,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *keys, 
         const uint64_t key = s_key[slot];
         const int d = (int)((key >> shift) & (kBins - 1));
         const int64_t pos = (int64_t)s_off[d] + (slot - s_start[d]);
-        keys_out[pos] = key;
-        vals_out[pos] = s_val[slot];
+        if (in_bounds(pos, n, BS_SORT_OUT)) {
+            keys_out[pos] = key;
+            vals_out[pos] = s_val[slot];
+        }
     }
 }
 
