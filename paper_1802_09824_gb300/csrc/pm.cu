@@ -90,11 +90,95 @@ __device__ __forceinline__ int pm_cell(double x, double L, double inv_dg, int N,
     return i;
 }
 
-template <int PT>
-__device__ __forceinline__ double load_coord(const void *pos, int64_t k)
+// The same for an FP32 coordinate without FP64: u = x N/L as a double-float
+// product -- x times the double-float (c_hi, c_lo) of N/L, the product's
+// rounding error taken exactly by an FMA -- the node from the high part and
+// the fraction from the exact difference of the high part and its floor
+// plus the low part (error ~2^-48 u in u, one FP32 rounding in f).  For x in
+// [0, L); the caller sends other coordinates through pm_cell.
+struct CellScale {
+    float c_hi, c_lo, L_up;   // N/L as c_hi + c_lo; L_up: an FP32 x is below L iff x < L_up
+};
+
+__device__ __forceinline__ int pm_cell32(float x, const CellScale &cs, int N, float &f)
 {
-    if (PT == PH_F64) return static_cast<const double *>(pos)[k];
-    return (double)static_cast<const float *>(pos)[k];
+    const float p = x * cs.c_hi;
+    const float e = fmaf(x, cs.c_hi, -p);   // x c_hi - p exactly
+    const float lo = fmaf(x, cs.c_lo, e);   // the rest of x N/L
+    float fl = floorf(p);
+    float fr = (p - fl) + lo;                // p - fl is exact
+    if (fr < 0.f) {
+        fr += 1.f;
+        fl -= 1.f;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        fl += 1.f;
+    }
+    int i = (int)fl;
+    if (i >= N) i -= N;
+    if (i < 0) i += N;
+    f = fr;
+    return i;
+}
+
+// Node and FP32 fraction of coordinate x: the FP32 path for an FP32 x in
+// [0, L), the FP64 one otherwise.
+template <int PT>
+__device__ __forceinline__ int pm_cell_any(const void *pos, int64_t k, double L, double inv_dg, const CellScale &cs,
+                                           int N, float &f)
+{
+    if (PT == PH_F32) {
+        const float x = static_cast<const float *>(pos)[k];
+        if (x >= 0.f && x < cs.L_up) return pm_cell32(x, cs, N, f);
+    }
+    double fd;
+    const int i = pm_cell(PT == PH_F32 ? (double)static_cast<const float *>(pos)[k] : static_cast<const double *>(pos)[k],
+                          L, inv_dg, N, fd);
+    f = (float)fd;
+    return i;
+}
+
+// Round a finite FP32 value to the nearest 64-bit integer (ties to even) with
+// integer operations (|v| < 2^63), from the binary32 format: the significand
+// shifted by the exponent.
+__device__ __forceinline__ long long f2ll_rn(float v)
+{
+    const unsigned int b = __float_as_uint(v) & 0x7FFFFFFFu;
+    const int e = (int)(b >> 23) - 127;   // v = 1.m 2^e
+    unsigned long long q = 0;
+    if (e >= 23) {
+        q = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << (e - 23);
+    } else if (e >= -1) {
+        const unsigned int m = (b & 0x7FFFFFu) | 0x800000u;
+        const int sh = 23 - e;            // 1 .. 24
+        const unsigned int qq = m >> sh, rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        q = qq + ((rem > half || (rem == half && (qq & 1u))) ? 1u : 0u);
+    }
+    return (__float_as_uint(v) >> 31) ? -(long long)q : (long long)q;
+}
+
+// A 64-bit integer (|q| < 2^63) to the nearest FP32 value (ties to even)
+// with integer operations.
+__device__ __forceinline__ float ll2f_rn(long long q)
+{
+    if (q == 0) return 0.f;
+    const unsigned int sign = q < 0 ? 0x80000000u : 0u;
+    unsigned long long a = q < 0 ? (unsigned long long)(-q) : (unsigned long long)q;
+    int e = 63 - __clzll((long long)a);   // a in [2^e, 2^(e+1))
+    unsigned long long m;
+    if (e <= 23) {
+        m = a << (23 - e);
+    } else {
+        const int sh = e - 23;
+        m = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) m++;
+        if (m == (1ull << 24)) {
+            m >>= 1;
+            e++;
+        }
+    }
+    return __uint_as_float(sign | ((unsigned int)(e + 127) << 23) | ((unsigned int)m & 0x7FFFFFu));
 }
 
 // Fixed-point scale 2^(62 - e) with n max|m| < 2^e: no node (nor the total)
@@ -104,6 +188,16 @@ __device__ __forceinline__ double pm_scale(const uint32_t *mmax_bits, int64_t n)
     const double b = (double)__uint_as_float(*mmax_bits) * (double)n;
     if (!(b > 0.0)) return 1.0;
     return ldexp(1.0, 62 - (ilogb(b) + 1));
+}
+
+// The exponent k of the scale 2^k, computed once per block (its FP64 steps
+// are slow on this GPU) and shared; values are scaled with ldexpf (exact).
+__device__ __forceinline__ int pm_scale_exp_block(const uint32_t *mmax_bits, int64_t n)
+{
+    __shared__ int s_k;
+    if (threadIdx.x == 0) s_k = ilogb(pm_scale(mmax_bits, n));
+    __syncthreads();
+    return s_k;
 }
 
 __global__ void k_pm_mass_max(const float *mass, int64_t n, float mass_default, uint32_t *mmax_bits,
@@ -123,32 +217,47 @@ __global__ void k_pm_mass_max(const float *mass, int64_t n, float mass_default, 
         best = max(best, __float_as_uint(fabsf(m)));
     }
     for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(mmax_bits, best);
+    // one atomic per block (the warps' maxima through shared memory)
+    __shared__ uint32_t s_best[kPmThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        best = threadIdx.x < (blockDim.x >> 5) ? s_best[threadIdx.x] : 0u;
+        for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (threadIdx.x == 0 && best) atomicMax(mmax_bits, best);
+    }
 }
 
 template <int PT>
 __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, float mass_default, double L,
-                             double inv_dg, int N, const uint32_t *mmax_bits, unsigned long long *mesh_q,
-                             uint32_t *status)
+                             double inv_dg, CellScale cs, int N, const uint32_t *mmax_bits,
+                             unsigned long long *mesh_q, uint32_t *status)
 {
-    const double S = pm_scale(mmax_bits, n);
+    const int kS = pm_scale_exp_block(mmax_bits, n);   // S = 2^kS: m S is exact in FP32
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = load_coord<PT>(pos, 3 * i), y = load_coord<PT>(pos, 3 * i + 1),
-                     z = load_coord<PT>(pos, 3 * i + 2);
-        const double m = mass ? (double)mass[i] : (double)mass_default;
-        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(m))) {
+        const float m = mass ? mass[i] : mass_default;
+        bool finite = isfinite(m);
+        if (PT == PH_F32) {
+            const float *p = static_cast<const float *>(pos) + 3 * i;
+            finite = finite && isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+        } else {
+            const double *p = static_cast<const double *>(pos) + 3 * i;
+            finite = finite && isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+        }
+        if (!finite) {
             atomicOr(status, ST_NONFINITE);
             continue;
         }
-        double fx, fy, fz;
-        const int ix = pm_cell(x, L, inv_dg, N, fx);
-        const int iy = pm_cell(y, L, inv_dg, N, fy);
-        const int iz = pm_cell(z, L, inv_dg, N, fz);
-        // weights and products in FP32 (this GPU's FP64 pipe is narrow): a
-        // node's share carries ~3 FP32 roundings, the integer sums none
-        const float gx = (float)fx, gy = (float)fy, gz = (float)fz;
+        // the node and fraction of each axis; the weights, the shares and
+        // their conversion to 64-bit fixed point in FP32 and integer
+        // operations (this GPU's FP64 pipe is narrow): a node's share carries
+        // ~3 FP32 roundings, the integer sums none
+        float gx, gy, gz;
+        const int ix = pm_cell_any<PT>(pos, 3 * i, L, inv_dg, cs, N, gx);
+        const int iy = pm_cell_any<PT>(pos, 3 * i + 1, L, inv_dg, cs, N, gy);
+        const int iz = pm_cell_any<PT>(pos, 3 * i + 2, L, inv_dg, cs, N, gz);
         const float wx[2] = {1.f - gx, gx}, wy[2] = {1.f - gy, gy};
-        const float mS = (float)(m * S);
+        const float mS = ldexpf(m, kS);
         const float wzm[2] = {(1.f - gz) * mS, gz * mS};
         const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
         const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
@@ -161,7 +270,7 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
                 const int64_t row = ((int64_t)jx[a] * N + jy[b]) * N;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const long long q = __float2ll_rn(wab * wzm[c]);
+                    const long long q = f2ll_rn(wab * wzm[c]);
                     if (q && in_bounds(row + jz[c], (int64_t)N * N * N, BS_PM_NODE))
                         atomicAdd(mesh_q + row + jz[c], (unsigned long long)q);
                 }
@@ -173,9 +282,9 @@ __global__ void k_pm_deposit(const void *pos, const float *mass, int64_t n, floa
 __global__ void k_pm_unfix(const unsigned long long *mesh_q, int64_t cells, int64_t n, const uint32_t *mmax_bits,
                            float *mesh_r)
 {
-    const float inv = (float)(1.0 / pm_scale(mmax_bits, n));   // a power of two
+    const int kS = pm_scale_exp_block(mmax_bits, n);   // S = 2^kS
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
-        mesh_r[i] = __ll2float_rn((long long)mesh_q[i]) * inv;
+        mesh_r[i] = ldexpf(ll2f_rn((long long)mesh_q[i]), -kS);
 }
 
 // Multiply the half spectrum by the filtered Green's function.  c0 folds
@@ -224,19 +333,24 @@ __global__ void k_pm_grad(const float *phi, int N, float c_half, float4 *mesh_a)
 }
 
 template <int PT>
-__global__ void k_pm_interp(const void *pos, int64_t n, double L, double inv_dg, int N, const float4 *mesh_a,
-                            float *acc, float *pot, int accumulate, const uint8_t *active)
+__global__ void k_pm_interp(const void *pos, int64_t n, double L, double inv_dg, CellScale cs, int N,
+                            const float4 *mesh_a, float *acc, float *pot, int accumulate, const uint8_t *active)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (active && !active[i]) continue;
-        const double x = load_coord<PT>(pos, 3 * i), y = load_coord<PT>(pos, 3 * i + 1),
-                     z = load_coord<PT>(pos, 3 * i + 2);
-        if (!(isfinite(x) && isfinite(y) && isfinite(z))) continue;   // latched by the deposit
-        double fx, fy, fz;
-        const int ix = pm_cell(x, L, inv_dg, N, fx);
-        const int iy = pm_cell(y, L, inv_dg, N, fy);
-        const int iz = pm_cell(z, L, inv_dg, N, fz);
-        const float gx = (float)fx, gy = (float)fy, gz = (float)fz;
+        bool finite;
+        if (PT == PH_F32) {
+            const float *p = static_cast<const float *>(pos) + 3 * i;
+            finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+        } else {
+            const double *p = static_cast<const double *>(pos) + 3 * i;
+            finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+        }
+        if (!finite) continue;   // latched by the deposit
+        float gx, gy, gz;
+        const int ix = pm_cell_any<PT>(pos, 3 * i, L, inv_dg, cs, N, gx);
+        const int iy = pm_cell_any<PT>(pos, 3 * i + 1, L, inv_dg, cs, N, gy);
+        const int iz = pm_cell_any<PT>(pos, 3 * i + 2, L, inv_dg, cs, N, gz);
         const float wx[2] = {1.f - gx, gx}, wy[2] = {1.f - gy, gy}, wz[2] = {1.f - gz, gz};
         const int jx[2] = {ix, ix + 1 == N ? 0 : ix + 1};
         const int jy[2] = {iy, iy + 1 == N ? 0 : iy + 1};
@@ -449,6 +563,11 @@ int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, con
     const int N = n_mesh;
     const int64_t cells = (int64_t)N * N * N;
     const double dg = p.L / N, inv_dg = (double)N / p.L;
+    CellScale cs;
+    cs.c_hi = (float)inv_dg;
+    cs.c_lo = (float)(inv_dg - (double)cs.c_hi);
+    cs.L_up = (float)p.L;
+    if ((double)cs.L_up < p.L) cs.L_up = std::nextafter(cs.L_up, INFINITY);
     const float mdef = (float)(1.0 / (double)n);
     uint32_t *st = static_cast<uint32_t *>(h->status.p);
     uint32_t *mmax = static_cast<uint32_t *>(h->scale.p);
@@ -458,9 +577,11 @@ int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, con
     if (rc) return rc;
     k_pm_mass_max<<<dmass ? grid_of(n) : 1, kPmThreads, 0, s>>>(dmass, n, mdef, mmax, st);
     if (pos_type == PH_F64)
-        k_pm_deposit<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, N, mmax, mq, st);
+        k_pm_deposit<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, cs, N, mmax, mq,
+                                                               st);
     else
-        k_pm_deposit<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, N, mmax, mq, st);
+        k_pm_deposit<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, dmass, n, mdef, p.L, inv_dg, cs, N, mmax, mq,
+                                                               st);
     float *mr = static_cast<float *>(h->mesh_r.p);
     k_pm_unfix<<<grid_of(cells), kPmThreads, 0, s>>>(mq, cells, n, mmax, mr);
     count_launch(3);
@@ -478,11 +599,11 @@ int ph_pm_accel(const void *pos, int pos_type, const float *mass, int64_t n, con
     float4 *ma = static_cast<float4 *>(h->mesh_a.p);
     k_pm_grad<<<grid_of(cells), kPmThreads, 0, s>>>(mr, N, (float)(-0.5 / dg), ma);
     if (pos_type == PH_F64)
-        k_pm_interp<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate,
-                                                              h->active);
+        k_pm_interp<PH_F64><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, cs, N, ma, dacc, dpot,
+                                                              accumulate, h->active);
     else
-        k_pm_interp<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, N, ma, dacc, dpot, accumulate,
-                                                              h->active);
+        k_pm_interp<PH_F32><<<grid_of(n), kPmThreads, 0, s>>>(dpos, n, p.L, inv_dg, cs, N, ma, dacc, dpot,
+                                                              accumulate, h->active);
     count_launch(2);
     rc = cuda_check(cudaGetLastError(), "PM kernels");
     if (!rc && host_acc)
