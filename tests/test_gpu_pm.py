@@ -199,3 +199,36 @@ def test_pm_positions_outside_the_box(gpu_lib):
     _check(b, ref)
     for h in (h1, h2):
         gpu_lib.ph_free(h)
+
+
+def test_pm_fp32_cell_arithmetic_matches_fp64(gpu_lib):
+    # FP32 coordinates take the double-float cell arithmetic, FP64 ones the
+    # FP64 path; on the same values (including coordinates exactly on
+    # nodes, one FP32 step below them, 0 and the largest FP32 value below L)
+    # the node masses and accelerations agree to FP32 rounding
+    import torch
+    B = gpu_lib
+    L, N = 100.0, 64
+    rng = np.random.default_rng(31)
+    x = rng.uniform(0.0, L, size=(20000, 3)).astype(np.float32)
+    nodes = (np.arange(N) * (L / N)).astype(np.float32)
+    x[:N, 0] = nodes
+    x[N:2 * N, 1] = np.nextafter(nodes, np.float32(-1.0))
+    x[2 * N:2 * N + 1] = 0.0
+    x[2 * N + 1:2 * N + 2] = np.nextafter(np.float32(L), np.float32(0.0))
+    x[:2 * N + 2] = np.where(x[:2 * N + 2] < 0, 0.0, x[:2 * N + 2])
+    m = rng.uniform(0.5, 1.5, size=20000).astype(np.float32)
+    prm = B.make_params(L, 1.0, 0.01, 1.25 * L / N, 4.5 * 1.25 * L / N)
+    out = {}
+    for dt in (torch.float32, torch.float64):
+        pos = torch.from_numpy(x).to(dt).cuda()
+        acc = torch.zeros((len(x), 3), device="cuda")
+        h = B.ph_pm_accel(pos, torch.from_numpy(m).cuda(), prm, N, acc)
+        torch.cuda.synchronize()
+        v = B.ph_pm_get_view(h)
+        out[dt] = (acc.cpu().numpy().astype(np.float64), v["mass_fixed"].cpu().numpy().astype(np.float64))
+        B.ph_free(h)
+    a32, q32 = out[torch.float32]
+    a64, q64 = out[torch.float64]
+    assert np.abs(q32 - q64).max() <= 1e-6 * np.abs(q64).max()
+    assert np.abs(a32 - a64).max() <= 1e-6 * np.abs(a64).max()
