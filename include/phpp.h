@@ -539,9 +539,12 @@ int ph_count_within(const ph_leaves *leaves, const ph_pairs *pairs, int64_t *n_w
  * PP inner loop (PH_G_LEARNED).  Input z0 = 2 r / rcut - 1; output g_hat(r).
  * Parameters, flat float32[321]: W1[16], b1[16], W2[16][16] (row k holds the
  * weights into unit k), b2[16], W3[16], b3.  Inference in the PP kernel:
- * layer 1 and the SiLUs in FP32 (SFU ex2/rcp), layer 2 as BF16 tensor-core
- * MMAs (mma.sync m16n8k16, FP32 accumulation, activations and weights split
- * into BF16 hi + lo parts).  A handle records the largest relative error of
+ * layer 1 (one scalar input) by linear interpolation in a 512-node table of
+ * its 16 activations that each kernel builds in shared memory from the
+ * weights, layer 2 as BF16 tensor-core MMAs (mma.sync m16n8k16, FP32
+ * accumulation, activations and weights split into BF16 hi + lo parts), its
+ * SiLUs in FP32 (SFU ex2/rcp) and layer 3 in FP32; only pairs with
+ * r < rcut are evaluated.  A handle records the largest relative error of
  * g_hat against the exact factor over r in [0, rcut) (the exact path judges
  * the network); ph_pp_accel falls back to the exact factor and returns
  * PH_WARN_FALLBACK when that error is above the handle's tolerance or the
