@@ -63,11 +63,13 @@ FLOPS_PER_INTERACTION = 44
 PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # DRAM traffic (read + write) of one PP launch on the 128^3 Zel'dovich lattice,
 # from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# k_pp launch of this benchmark's configuration: leaf_max 32, binary levels,
-# kernel shape 0, 32-particle groups, Peano-Hilbert keys.  None for any other
-# configuration, or once the kernel has changed since the capture.
+# k_pp launch of this benchmark's configurations the autotuner picks between:
+# leaf_max 32 or 16, binary levels, kernel shape 0, 32-particle groups,
+# Peano-Hilbert keys.  None for any other configuration, or once the kernel
+# has changed since the capture.
 PP_TRAFFIC = {   # (workload, scale, leaf_max, levels, variant, group, key) -> bytes
     ("zeldovich_128", 0, 32, 1, 0, 32, 1): 194206720 + 18382080,
+    ("zeldovich_128", 0, 16, 1, 0, 32, 1): 263585280 + 19879680,
 }
 
 
@@ -471,6 +473,20 @@ def _batched_extra(B, args, dev, stream):
     torch.cuda.synchronize()
     B.ph_status(pr)
     t_graph = e0.elapsed_time(e1) / reps
+    # the PP kernel alone on the batch's lists (one persistent launch over
+    # all boxes' groups), its FP32 roofline and the within-R_cut share
+    e0.record(stream)
+    for _ in range(reps):
+        B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pp = e0.elapsed_time(e1) / reps
+    inter, _ = B.ph_pp_counters(pr)
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * 2 * 2070.0 * 1e6 / 1e12
+    pp = {"ms": t_pp, "interactions_evaluated": inter, "within_fraction": n_within / max(inter, 1),
+          "roofline_frac": inter * FLOPS_PER_INTERACTION / (t_pp * 1e-3) / 1e12 / peak,
+          "peak_tflops": peak}
     # the same boxes, each its own captured step (same knobs), replayed one
     # after another on the stream
     views = [(pos[ps.box_slice(b)], mass[ps.box_slice(b)], acc[ps.box_slice(b)]) for b in range(len(ps.boxes))]
@@ -519,7 +535,7 @@ def _batched_extra(B, args, dev, stream):
             "tuned": {"leaf_max": p0.leaf_max, "level_bits": p0.level_bits, "pp_variant": p0.pp_variant,
                       "group_size": p0.group_size or 32, "key_kind": p0.key_kind, "cache": tune_info["cache"],
                       "tune_s": tune_s},
-            "graph_ms_per_step": t_graph, "graph_kernels_per_step": kernels,
+            "graph_ms_per_step": t_graph, "graph_kernels_per_step": kernels, "pp": pp,
             "per_box_graphs_ms_per_step": t_graphs, "speedup_graph_vs_per_box_graphs": t_graphs / t_graph,
             "per_box_calls_ms_per_step": t_box, "speedup_graph_vs_per_box_calls": t_box / t_graph,
             "value_graph": n_within / (t_graph * 1e-3), "unit": UNIT}
