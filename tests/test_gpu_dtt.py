@@ -11,14 +11,14 @@ from paper_1802_09824_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _run(B, ps, theta, leaf_max=16, gs=0):
+def _run(B, ps, theta, leaf_max=16, gs=0, g_mode=None):
     import torch
     bp = ps.boxes[0]
     prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, leaf_max, 0, gs, 0, 0, theta)
     lv = B.ph_build_leaves(torch.from_numpy(ps.pos).cuda(), torch.from_numpy(ps.mass).cuda(), prm)
     pr = B.ph_leaf_pairs(lv)
     acc = torch.zeros((ps.n, 3), dtype=torch.float32, device="cuda")
-    B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc)
+    B.ph_pp_accel(lv, pr, B.PH_G_EXACT if g_mode is None else g_mode, None, acc)
     torch.cuda.synchronize()
     v = B.ph_leaves_get_view(lv)
     pv = B.ph_pairs_get_view(pr)
@@ -70,5 +70,19 @@ def test_tree_part_matches_its_oracle(gpu_lib, name, scale, theta, leaf_max, gs)
     # agree up to the ambiguous ones
     assert r.n_accepted - r.n_ambiguous <= n_mono <= 1.02 * (r.n_accepted + r.n_ambiguous) + 10
     assert r.n_ambiguous <= 1e-3 * r.n_accepted + 10
+    res = force.AccelResult(acc=r.acc, abs_sum=None, n_within=None, near_abs=r.near_abs + r.amb_abs)
+    check_parity(got, res)
+
+
+def test_tree_part_with_the_tabulated_factor(gpu_lib):
+    """The tree part's mass-centre bodies go through the PP kernel like any
+    source, so the tabulated factor (Sec. 3.1's table) applies to them too:
+    the same parity with the tree oracle (exact factor), the table's own
+    error (~6e-7 of a term) far inside the tolerance."""
+    ps = synth.workload("nfw_mix_256", scale=20)
+    got, n_mono, T, _ = _run(gpu_lib, ps, 0.3, 16, 0, g_mode=gpu_lib.PH_G_TABLE)
+    bp = ps.boxes[0]
+    r = dtt.accel(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 0.3, leaf_max=16, group_size=32, T=T)
+    assert n_mono > 0 and r.n_accepted > 0
     res = force.AccelResult(acc=r.acc, abs_sum=None, n_within=None, near_abs=r.near_abs + r.amb_abs)
     check_parity(got, res)

@@ -99,6 +99,30 @@ def test_learned_pp_matches_oracle_with_the_same_network(gpu_lib, trained):
         B.ph_free(x)
 
 
+def test_learned_pp_matches_oracle_on_a_clustered_box(gpu_lib, trained):
+    # the NFW mixture (dense haloes: long source lists, many pairs within
+    # R_cut per group, so the ring of pending pairs fills and drains often)
+    B = gpu_lib
+    h, w, err, loss = trained
+    ps = synth.workload("nfw_mix_256", scale=20)
+    bp = ps.boxes[0]
+    m = B.ph_mlp_create(w, bp.rs, bp.rcut, tol=1.0)
+    import torch
+    pos = torch.from_numpy(ps.pos).cuda()
+    mass = torch.from_numpy(ps.mass).cuda()
+    acc = torch.zeros((ps.n, 3), device="cuda")
+    prm = B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 16)
+    lv, pr = B.ph_accel(pos, mass, prm, B.PH_G_LEARNED, m, acc)
+    got = acc.cpu().numpy().astype(np.float64)
+    ref = force.accel_mlp(ps.pos, ps.mass, bp.L, bp.G, bp.eps, bp.rcut, w.astype(np.float64))
+    am = np.linalg.norm(ref, axis=1)
+    e = np.linalg.norm(got - ref, axis=1) / np.maximum(am, 1e-3 * np.median(am))
+    print(f"learned PP vs oracle(network), NFW mixture: p99 {np.percentile(e, 99):.2e} max {e.max():.2e}")
+    assert np.percentile(e, 99) <= 1e-4 and e.max() <= 1e-3
+    for x in (pr, lv, m):
+        B.ph_free(x)
+
+
 @pytest.mark.parametrize("gs", [8, 16])
 def test_learned_pp_smaller_groups(gpu_lib, trained, gs):
     # 16- and 8-particle target groups (2 or 4 lanes per target, each taking
