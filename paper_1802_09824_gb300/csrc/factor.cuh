@@ -49,13 +49,15 @@ __device__ __forceinline__ f2_t pk(float lo, float hi)
 }
 __device__ __forceinline__ float lo_of(f2_t v)
 {
-    float lo, hi;
+    float lo;
+    [[maybe_unused]] float hi;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
     return lo;
 }
 __device__ __forceinline__ float hi_of(f2_t v)
 {
-    float lo, hi;
+    [[maybe_unused]] float lo;
+    float hi;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
     return hi;
 }
