@@ -246,6 +246,21 @@ int ph_graph_launch(ph_graph *graph, void *stream);
  */
 int ph_graph_launch_host(ph_graph *graph, const void *h_pos, const float *h_mass, float *h_acc, void *stream);
 
+/*
+ * The same work as ph_graph_launch_host -- the copies in, the replay, the
+ * copy out -- enqueued on `stream` without waiting for it.  h_acc holds the
+ * step's accelerations once the stream has passed this work (synchronise
+ * it); h_pos and h_mass must stay unchanged until then.  Device conditions
+ * (capacity, non-finite input) are latched in the handles' status words:
+ * read them with ph_status on the leaves and pairs after synchronising.
+ * With pinned host memory, two graphs over separate handles and device
+ * buffers replayed alternately on two streams overlap one step's copies
+ * with the other's kernels.  Errors: PH_ERR_ARG, PH_ERR_STATE (as
+ * ph_graph_launch), PH_ERR_CUDA.
+ */
+int ph_graph_launch_host_async(ph_graph *graph, const void *h_pos, const float *h_mass, float *h_acc,
+                               void *stream);
+
 /* Kernels launched by one replay. */
 int ph_graph_kernels(const ph_graph *graph, int64_t *kernels);
 

@@ -136,6 +136,7 @@ _SIGS = {
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_graph_launch": ([_VP, _VP], ctypes.c_int),
     "ph_graph_launch_host": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "ph_graph_launch_host_async": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "ph_graph_kernels": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ph_pm_accel": ([_VP, ctypes.c_int, _VP, ctypes.c_int64, ctypes.POINTER(ph_params), ctypes.c_int32, _VP, _VP,
                      ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -442,6 +443,12 @@ def ph_graph_launch(graph, stream=None):
 def ph_graph_launch_host(graph, pos, mass, acc, stream=None):
     """Copy host pos/mass in, replay, copy acc out (synchronises)."""
     return _check(lib().ph_graph_launch_host(graph.ptr, _ptr(pos), _ptr(mass), _ptr(acc), _stream(stream)))
+
+
+def ph_graph_launch_host_async(graph, pos, mass, acc, stream=None):
+    """Enqueue the copies in, the replay and the copy out without waiting;
+    acc is valid after the stream is synchronised (pinned host tensors)."""
+    return _check(lib().ph_graph_launch_host_async(graph.ptr, _ptr(pos), _ptr(mass), _ptr(acc), _stream(stream)))
 
 
 def ph_graph_kernels(graph):

@@ -186,6 +186,26 @@ int ph_graph_launch_host(ph_graph *g, const void *h_pos, const float *h_mass, fl
     return PH_OK;
 }
 
+int ph_graph_launch_host_async(ph_graph *g, const void *h_pos, const float *h_mass, float *h_acc, void *stream)
+{
+    TraceRange trace_("ph_graph_launch_host_async");
+    if (!g || g->kind != KIND_GRAPH) return fail(PH_ERR_ARG, "not a ph_graph handle");
+    if (g->n > 0 && (!h_pos || !h_acc)) return fail(PH_ERR_ARG, "h_pos and h_acc must not be NULL");
+    if (h_mass && !g->d_mass) return fail(PH_ERR_ARG, "the graph was captured without masses");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)g->n;
+    const size_t pbytes = n * 3 * (g->pos_type == PH_F64 ? 8 : 4);
+    int rc = PH_OK;
+    if (n) rc = cuda_check(cudaMemcpyAsync(const_cast<void *>(g->d_pos), h_pos, pbytes, cudaMemcpyDefault, s),
+                           "copy positions");
+    if (!rc && n && h_mass)
+        rc = cuda_check(cudaMemcpyAsync(const_cast<float *>(g->d_mass), h_mass, n * 4, cudaMemcpyDefault, s),
+                        "copy masses");
+    if (!rc) rc = ph_graph_launch(g, stream);
+    if (!rc && n) rc = cuda_check(cudaMemcpyAsync(h_acc, g->d_acc, n * 12, cudaMemcpyDefault, s), "copy acc");
+    return rc;
+}
+
 int ph_graph_kernels(const ph_graph *g, int64_t *kernels)
 {
     if (!g || g->kind != KIND_GRAPH || !kernels) return fail(PH_ERR_ARG, "bad arguments");

@@ -118,6 +118,46 @@ def test_graph_replay_with_host_buffers(gpu_lib):
         B.ph_free(h)
 
 
+def test_overlapped_host_replays_on_two_streams(gpu_lib):
+    # ph_graph_launch_host_async: two graphs over separate handles and
+    # buffers, replayed alternately on two streams from pinned host buffers
+    # holding two different particle sets; every step's result equals a
+    # synchronous replay of the same set, bit for bit
+    import torch
+    B = gpu_lib
+    ps = synth.workload("uniform_small", scale=5000)
+    prm = _params(B, ps)[0]
+    rng = np.random.default_rng(8)
+    inputs = [ps.pos.copy(), np.mod(ps.pos + rng.uniform(0, 0.01, ps.pos.shape), 1.0).astype(np.float32)]
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    sets, refs = [], []
+    for i in range(2):
+        pos, mass, acc = _tensors(ps)
+        pos.copy_(torch.from_numpy(inputs[i]))
+        torch.cuda.synchronize()
+        lv = B.ph_build_leaves(pos, mass, prm, streams[i])
+        pr = B.ph_leaf_pairs(lv, streams[i])
+        g = B.ph_graph_create(lv, pr, pos, mass, B.PH_G_EXACT, None, acc, headroom=0.25, stream=streams[i])
+        hp = torch.from_numpy(inputs[i].copy()).pin_memory()
+        hm = torch.from_numpy(ps.mass.copy()).pin_memory()
+        ha = torch.full((ps.n, 3), float("nan")).pin_memory()
+        B.ph_graph_launch_host(g, hp, hm, ha, streams[i])
+        refs.append(ha.numpy().copy())
+        sets.append((g, pr, lv, hp, hm, ha, streams[i]))
+    assert not np.array_equal(refs[0], refs[1])
+    for k in range(6):
+        g, pr, lv, hp, hm, ha, s = sets[k % 2]
+        B.ph_graph_launch_host_async(g, hp, hm, ha, s)
+    torch.cuda.synchronize()
+    for i in range(2):
+        g, pr, lv, hp, hm, ha, s = sets[i]
+        B.ph_status(lv)
+        B.ph_status(pr)
+        np.testing.assert_array_equal(ha.numpy(), refs[i])
+        for h in (g, pr, lv):
+            B.ph_free(h)
+
+
 @pytest.mark.parametrize("gs", [8, 16, 32])
 def test_group_sizes_match_the_oracle(gpu_lib, gs):
     ps = synth.workload("zeldovich_128", scale=32)
