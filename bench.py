@@ -827,6 +827,18 @@ def run_ours(args, rank, world, local_rank):
                                 "pair_tests_per_s_per_core": tests_per_s / cores,
                                 "extrapolated_full_step_s": float(ps.n) * ps.n / tests_per_s,
                                 "extrapolated": "all N targets at the sample's rate"}
+        # the small configuration (4096 uniform particles) in full: every
+        # target against every source, no extrapolation
+        from oracle import force
+        small = synth.workload("uniform_small")
+        sb = small.boxes[0]
+        t0 = time.perf_counter()
+        rs_ = force.accel(small.pos, small.mass, sb.L, sb.G, sb.eps, sb.rs, sb.rcut)
+        dts = time.perf_counter() - t0
+        line["cpu_baseline"]["small_config_full"] = {
+            "workload": "uniform_small", "n": small.n, "s": dts,
+            "interactions_per_s": float(rs_.n_within.sum()) / dts,
+            "pair_tests_per_s_per_core": float(small.n) * small.n / dts / cores}
     # the paper's PP kernel efficiencies (fraction of the node's peak, Sec. 5):
     # other hardware and a 22-flop convention, context only
     line["paper_context"] = {"pp_efficiency_cpu": 0.744, "pp_efficiency_mic": 0.686,
