@@ -686,6 +686,22 @@ def run_ours(args, rank, world, local_rank):
         pevs[k][1].record(stream)
     torch.cuda.synchronize()
     t_pp = sum(e[0].elapsed_time(e[1]) for e in pevs) / args.steps
+    # the leaf build and the pair list alone (direct calls on the same
+    # handles, L2 flushed first; CUDA events on the stream, so the pair
+    # call's host read of its list size is inside its interval)
+    tb, tq = [], []
+    for _ in range(max(args.steps // 2, 5)):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        lv = B.ph_build_leaves(pos, mass, prm, stream, leaves=lv)
+        ev[1].record(stream)
+        pr = B.ph_leaf_pairs(lv, stream, pairs=pr)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        tb.append(ev[0].elapsed_time(ev[1]))
+        tq.append(ev[1].elapsed_time(ev[2]))
+    t_build, t_pairs = float(np.median(tb)), float(np.median(tq))
 
     # ---- end to end through the public calls with host buffers: the
     # captured step replayed from pinned host buffers (ph_graph_launch_host:
@@ -804,6 +820,7 @@ def run_ours(args, rank, world, local_rank):
                "staged_sources": staged, "paper_convention_tflops": computed * PAPER_FLOPS_PER_INTERACTION /
                (t_pp * 1e-3) / 1e12},
         "build_and_pairs_ms": t_step - t_pp,
+        "build_ms": t_build, "pairs_ms": t_pairs,
     }
     if tune_info is not None:
         line["config"]["tuned"] = {"leaf_max": prm.leaf_max, "level_bits": prm.level_bits,
