@@ -592,6 +592,13 @@ int ph_mlp_create(const float *weights, double rs, double rcut, float tol, void 
 /* Weights (host float[321], nullable), validated error and last training loss. */
 int ph_mlp_get(const ph_mlp *mlp, float *weights, float *max_rel_err, float *last_loss);
 
+/* g_hat at n inputs z0 = 2r/rcut - 1 (device float[n] in, device float[n]
+ * out), evaluated exactly as the learned PP kernel does (layer-1 table,
+ * BF16 tensor-core layer 2, FP32 SiLUs and layer 3), for tests and
+ * inspection.  Asynchronous on `stream`.  Errors: PH_ERR_ARG (bad handle or
+ * pointers, host buffers), PH_ERR_CUDA. */
+int ph_mlp_eval(const ph_mlp *mlp, const float *d_z0, int64_t n, float *d_out, void *stream);
+
 /* One forward + backward pass of the training kernel on given inputs
  * (host or device float[n] each): gradient of the mean relative squared
  * error (host float[321]) and the loss.  Synchronises. */

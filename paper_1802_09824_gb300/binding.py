@@ -131,6 +131,7 @@ _SIGS = {
     "ph_mlp_save": ([_VP, ctypes.c_char_p], ctypes.c_int),
     "ph_mlp_load": ([ctypes.c_char_p, ctypes.c_float, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "ph_debug_fail_allocation": ([ctypes.c_int64], None),
+    "ph_mlp_eval": ([_VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "ph_debug_bounds": ([ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "ph_graph_create": ([_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP,
                          ctypes.POINTER(_VP)], ctypes.c_int),
@@ -360,6 +361,12 @@ def ph_mlp_create(weights, rs, rcut, tol=0.0, stream=None):
     w = np.ascontiguousarray(np.asarray(weights, np.float32))
     _check(lib().ph_mlp_create(_ptr(w), float(rs), float(rcut), float(tol), _stream(stream), ctypes.byref(out)))
     return Handle(out.value)
+
+
+def ph_mlp_eval(mlp, z0, out, stream=None):
+    """g_hat at the inputs z0 (device float32 tensor) into out, as the
+    learned PP kernel evaluates it."""
+    return _check(lib().ph_mlp_eval(mlp.ptr, _ptr(z0), int(z0.numel()), _ptr(out), _stream(stream)))
 
 
 def ph_mlp_get(mlp):

@@ -257,6 +257,27 @@ __global__ void k_validate(const float *theta, FactorConsts fc, int n_grid, unsi
     if ((threadIdx.x & 31) == 0) atomicMax(max_err_bits, __float_as_uint(worst));
 }
 
+// g_hat at caller-given inputs z0 (device array), by the same warp-level
+// evaluation as the learned PP kernel (layer-1 table, BF16 tensor cores).
+__global__ void k_eval(const float *theta, const float *z0, int64_t n, float *out)
+{
+    __shared__ float w[kMlpParams];
+    __shared__ float4 tab[4 * kL1Nodes];
+    for (int e = threadIdx.x; e < kMlpParams; e += blockDim.x) w[e] = theta[e];
+    __syncthreads();
+    l1_table_fill(w, tab);
+    __syncthreads();
+    MlpLane L;
+    mlp_lane_load(w, L);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += warps * 32) {
+        const int64_t k = base + (threadIdx.x & 31);
+        const float t = k < n ? z0[k] : -1.f;   // (the evaluation is warp-wide: idle lanes take t = -1)
+        const float gh = mlp_warp_eval(t, L, tab);
+        if (k < n) out[k] = gh;
+    }
+}
+
 FactorConsts factor_consts(double rs, double rcut)
 {
     FactorConsts fc;
@@ -517,6 +538,21 @@ int ph_mlp_train(const ph_train_params *tp, double rs, double rcut, const float 
     h->steps_done = tp->steps;
     *mlp = h;
     return PH_OK;
+}
+
+int ph_mlp_eval(const ph_mlp *h, const float *d_z0, int64_t n, float *d_out, void *stream)
+{
+    TraceRange trace_("ph_mlp_eval");
+    if (!h || h->kind != KIND_MLP) return fail(PH_ERR_ARG, "not a ph_mlp handle");
+    if (n < 0 || (n > 0 && (!d_z0 || !d_out))) return fail(PH_ERR_ARG, "bad arguments");
+    if (n > 0 && (!is_device_ptr(d_z0) || !is_device_ptr(d_out))) return fail(PH_ERR_ARG, "device buffers only");
+    if (n == 0) return PH_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t warps = (n + 31) / 32;
+    const int grid = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
+    k_eval<<<grid, 256, 0, s>>>(static_cast<const float *>(h->theta.p), d_z0, n, d_out);
+    count_launch();
+    return cuda_check(cudaGetLastError(), "network evaluation");
 }
 
 int ph_mlp_get(const ph_mlp *h, float *weights, float *max_rel_err, float *last_loss)

@@ -99,6 +99,38 @@ def test_learned_pp_matches_oracle_with_the_same_network(gpu_lib, trained):
         B.ph_free(x)
 
 
+def test_network_inference_matches_the_oracle_network(gpu_lib, trained):
+    """ph_mlp_eval (the learned PP kernel's own evaluation: layer 1 from the
+    512-node table, layer 2 as BF16 hi/lo tensor-core products) against the
+    oracle's FP64 forward pass of the same weights, point by point within
+    the analytic error budget: the table's linear interpolation,
+    (D^2/8) w1^2/2 per layer-1 unit with D = 2/511, and the BF16 hi/lo
+    splits of layer 2's operands (2^-15 of |W2| |h1| per unit), each carried
+    through layer 2's SiLU (slope <= 1.1) and |W3|."""
+    import torch
+    from oracle import mlp as omlp
+    B = gpu_lib
+    h, w, err, loss = trained
+    t = np.concatenate([np.linspace(-1.0, 1.0, 200001), [np.nextafter(np.float32(1.0), np.float32(0.0))]])
+    t = t.astype(np.float32)
+    out = torch.empty(t.size, device="cuda")
+    B.ph_mlp_eval(h, torch.from_numpy(t).cuda(), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    w64 = w.astype(np.float64)
+    ref, (_, a1, h1, a2, h2) = omlp.forward(w64, t.astype(np.float64))
+    W1, W2, W3 = w64[:16], w64[32:288].reshape(16, 16), w64[304:320]
+    D = 2.0 / 511
+    e_table = (D * D / 8) * W1 * W1 / 2                         # per layer-1 unit
+    e_split = 2.0 ** -15 * (np.abs(h1) @ np.abs(W2).T)           # per layer-2 unit and sample
+    e_pre = (np.abs(W2) @ e_table)[None, :] + e_split           # layer-2 pre-activation
+    bound = 1.1 * (e_pre @ np.abs(W3)) + 1e-6 * (1.0 + np.abs(ref))
+    d = np.abs(got - ref)
+    print(f"network inference vs FP64: max {d.max():.2e}, p99 {np.percentile(d, 99):.2e}, "
+          f"max / bound {np.max(d / bound):.2f}")
+    assert np.all(d <= bound), (int(np.argmax(d / bound)), float(np.max(d / bound)))
+
+
 def test_learned_pp_matches_oracle_on_a_clustered_box(gpu_lib, trained):
     # the NFW mixture (dense haloes: long source lists, many pairs within
     # R_cut per group, so the ring of pending pairs fills and drains often)
