@@ -99,6 +99,14 @@ extern "C" {
  *   pp_variant PP kernel shape: 0 = two 8-warp blocks per SM (deeper
  *             unrolled source loop), 1 = three blocks per SM (fewer
  *             registers, more warps).  Same results.
+ *   queue_order order in which the PP kernel's warps take the target groups
+ *             (the task queue of Sec. 4.3): 0 (default) = by decreasing
+ *             cost, the source particles of the group's list (Sec. 4.4
+ *             weighs work by counts), in quarter-octave classes, ties in
+ *             group order -- the heaviest groups start first, so the
+ *             launch ends on short ones; 1 = plain group order (along the
+ *             curve).  Same results (each group is summed by one warp on
+ *             its own).  Direct mode (no stored list) takes group order.
  *   theta     opening criterion of the tree part (Sec. 3.3), in [0, 1):
  *             0 (default) = every leaf pair by PP (the exact short-range
  *             sum); theta > 0 = a leaf for which both opening angles
@@ -122,7 +130,7 @@ typedef struct ph_params {
     int32_t group_size;
     int32_t level_bits;
     int32_t pp_variant;
-    int32_t reserved;
+    int32_t queue_order;
     double  theta;
 } ph_params;
 
@@ -520,6 +528,8 @@ typedef struct ph_pairs_view {
     const float   *entries;    /* [n_pairs*4] off.x, off.y, off.z, and the     */
                                /* leaf's first particle (int32 bits, sorted)   */
     const uint8_t *counts;     /* [n_pairs] particles in the leaf minus one    */
+    const int32_t *group_order;/* [n_groups] the PP queue's order of the groups
+                                  (queue_order 0), or NULL (group order)      */
 } ph_pairs_view;
 
 int ph_leaves_get_view(const ph_leaves *leaves, ph_leaves_view *out);

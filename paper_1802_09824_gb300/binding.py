@@ -44,7 +44,7 @@ class ph_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("G", ctypes.c_double), ("eps", ctypes.c_double),
                 ("rs", ctypes.c_double), ("rcut", ctypes.c_double), ("leaf_max", ctypes.c_int32),
                 ("key_kind", ctypes.c_int32), ("group_size", ctypes.c_int32), ("level_bits", ctypes.c_int32),
-                ("pp_variant", ctypes.c_int32), ("reserved", ctypes.c_int32), ("theta", ctypes.c_double)]
+                ("pp_variant", ctypes.c_int32), ("queue_order", ctypes.c_int32), ("theta", ctypes.c_double)]
 
 
 class ph_leaves_view(ctypes.Structure):
@@ -77,7 +77,8 @@ class ph_tune_result(ctypes.Structure):
 
 class ph_pairs_view(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+                ("group_off", ctypes.c_void_p), ("entries", ctypes.c_void_p), ("counts", ctypes.c_void_p),
+                ("group_order", ctypes.c_void_p)]
 
 
 class ph_pm_view(ctypes.Structure):
@@ -216,9 +217,9 @@ def _pos_type(t):
 
 
 def make_params(L, G, eps, rs, rcut, leaf_max=32, key_kind=PH_KEY_MORTON, group_size=0, level_bits=0,
-                pp_variant=0, theta=0.0):
+                pp_variant=0, theta=0.0, queue_order=0):
     return ph_params(float(L), float(G), float(eps), float(rs), float(rcut), int(leaf_max), int(key_kind),
-                     int(group_size), int(level_bits), int(pp_variant), 0, float(theta))
+                     int(group_size), int(level_bits), int(pp_variant), int(queue_order), float(theta))
 
 
 class Handle:
@@ -675,4 +676,5 @@ def ph_pairs_get_view(pairs):
         "group_off": _dev(v.group_off, (v.n_groups + 1,), "<i8"),
         "entries": _dev(v.entries, (v.n_pairs, 4), "<f4"),
         "counts": _dev(v.counts, (v.n_pairs,), "|u1"),
+        "group_order": _dev(v.group_order, (v.n_groups,), "<i4") if v.group_order else None,
     }

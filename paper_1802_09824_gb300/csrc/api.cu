@@ -201,6 +201,7 @@ static int check_params(const ph_params &p, int b)
     if (p.level_bits != 0 && p.level_bits != 1 && p.level_bits != 3)
         return fail(PH_ERR_ARG, "box %d: level_bits must be 0, 1 or 3", b);
     if (p.pp_variant != 0 && p.pp_variant != 1) return fail(PH_ERR_ARG, "box %d: pp_variant must be 0 or 1", b);
+    if (p.queue_order != 0 && p.queue_order != 1) return fail(PH_ERR_ARG, "box %d: queue_order must be 0 or 1", b);
     if (!(std::isfinite(p.theta) && p.theta >= 0 && p.theta < 1))
         return fail(PH_ERR_ARG, "box %d: theta must be in [0, 1)", b);
     if (poly_degree_for(p.rcut / (2.0 * p.rs)) < 0)
@@ -270,7 +271,8 @@ uint64_t buffers_fingerprint(const ph_leaves *h, const ph_pairs *p)
     }
     fp_mix(f, (uint64_t)h->n);
     if (p) {
-        const DevBuf *pb[] = {&p->group_cnt, &p->group_off, &p->entries, &p->ecount, &p->work, &p->status, &p->temp};
+        const DevBuf *pb[] = {&p->group_cnt, &p->group_off, &p->entries, &p->ecount, &p->work, &p->status, &p->temp,
+                              &p->group_key, &p->group_order, &p->order_temp};
         for (const DevBuf *b : pb) {
             fp_mix(f, (uint64_t)(uintptr_t)b->p);
             fp_mix(f, (uint64_t)b->bytes);
@@ -294,8 +296,13 @@ static void free_leaves(ph_leaves *h)
 static void free_pairs(ph_pairs *h)
 {
     DevBuf *bufs[] = {&h->group_cnt, &h->group_off, &h->entries, &h->ecount, &h->work, &h->status, &h->temp,
-                      &h->acc_tmp};
+                      &h->acc_tmp, &h->group_key, &h->group_order, &h->order_temp};
     for (DevBuf *b : bufs) release(*b);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
+    h->ev_fork = h->ev_join = nullptr;
+    h->side = nullptr;
 }
 
 // Set up boxes and buffers for n particles, copy host inputs, launch the build.
@@ -317,9 +324,9 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
         if (rc) return rc;
         if (params[b].leaf_max != params[0].leaf_max || params[b].key_kind != params[0].key_kind ||
             params[b].group_size != params[0].group_size || params[b].level_bits != params[0].level_bits ||
-            params[b].pp_variant != params[0].pp_variant)
-            return fail(PH_ERR_ARG,
-                        "leaf_max, key_kind, group_size, level_bits and pp_variant must be the same for all boxes");
+            params[b].pp_variant != params[0].pp_variant || params[b].queue_order != params[0].queue_order)
+            return fail(PH_ERR_ARG, "leaf_max, key_kind, group_size, level_bits, pp_variant and queue_order must be "
+                                    "the same for all boxes");
     }
     ph_leaves *h = *leaves;
     if (h && h->kind != KIND_LEAVES) return fail(PH_ERR_STATE, "handle is not a ph_leaves");
@@ -347,6 +354,7 @@ static int leaves_common(const void *pos, int pos_type, const float *mass, const
     h->group_size = params[0].group_size ? params[0].group_size : kDefaultGroup;
     h->level_bits = params[0].level_bits ? params[0].level_bits : 1;
     h->pp_variant = params[0].pp_variant;
+    h->queue_order = params[0].queue_order;
     h->boxes_host.resize(nb);
     int deg = 10;
     for (int b = 0; b < nb; b++) {
@@ -548,6 +556,28 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
     if (!rc) rc = ensure(p->group_off, 8 * (N + 1));
     if (!rc) rc = ensure(p->work, 64);
     if (!rc) rc = ensure(p->temp, scan_temp_bytes((int64_t)N));
+    if (!rc && leaves->queue_order == 0) {
+        rc = ensure(p->group_key, N);
+        if (!rc) rc = ensure(p->group_order, 4 * N);
+        if (!rc) rc = ensure(p->order_temp, order_temp_bytes((int64_t)N));
+        if (!rc && !p->side) {
+            // the order's stream and its fork / join events (made here, never
+            // inside a capture); without them the order runs on `stream`
+            cudaStream_t side = nullptr;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess) {
+                p->side = side;
+                p->ev_fork = e0;
+                p->ev_join = e1;
+            } else {
+                if (e0) cudaEventDestroy(e0);
+                if (side) cudaStreamDestroy(side);
+                cudaGetLastError();
+            }
+        }
+    }
     if (!rc && !p->status.p) {
         rc = ensure(p->status, 16);
         if (!rc) rc = cuda_check(cudaMemsetAsync(p->status.p, 0, 16, s), "status reset");
@@ -757,6 +787,7 @@ int ph_pairs_get_view(const ph_pairs *p, ph_pairs_view *out)
     out->group_off = static_cast<const int64_t *>(p->group_off.p);
     out->entries = static_cast<const float *>(p->entries.p);
     out->counts = static_cast<const uint8_t *>(p->ecount.p);
+    out->group_order = p->ordered ? static_cast<const int32_t *>(p->group_order.p) : nullptr;
     return PH_OK;
 }
 

@@ -28,6 +28,7 @@ enum BoundsSite : uint32_t {
     BS_BUILD_ROW = 11,    // build: leaf / group row
     BS_PM_NODE = 12,      // PM: mesh node
     BS_DOM_ROW = 13,      // device exchange: row of the send or receive buffer
+    BS_ORDER = 14,        // group order: output slot
 };
 
 #ifdef PHPP_BOUNDS_CHECK

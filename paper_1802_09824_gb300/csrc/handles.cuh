@@ -23,6 +23,7 @@ struct ph_leaves {
     int32_t key_kind = PH_KEY_MORTON;
     int32_t level_bits = 1;      // key bits per level of the leaf hierarchy (1 or 3)
     int32_t pp_variant = 0;      // PP kernel register/occupancy variant (0: 2 blocks/SM, 1: 3)
+    int32_t queue_order = 0;     // PP queue: 0 = groups by decreasing cost, 1 = group order
     bool tree_leaves = false;    // some box has theta > 0: leaf mass-centre particles are made
     std::vector<phpp::BoxDev> boxes_host;
     // device buffers
@@ -90,6 +91,16 @@ struct ph_pairs {
     phpp::DevBuf status;         // uint32
     phpp::DevBuf temp;
     phpp::DevBuf acc_tmp;        // float[3n] when the caller passes host memory
+    // the PP queue's order (groups by decreasing cost), made by the count
+    // pass when these buffers exist; `ordered` says the last list has it
+    phpp::DevBuf group_key;      // uint8[n]: 255 - cost bucket
+    phpp::DevBuf group_order;    // int32[n]: groups in queue order
+    phpp::DevBuf order_temp;     // histograms and scan scratch
+    bool ordered = false;
+    // the order is made on a second stream while the fill pass runs (joined
+    // back before the list is complete); null: on the caller's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace phpp {

@@ -173,6 +173,9 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, const int32_t
 int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, const int32_t *d_n, void *temp,
                        cudaStream_t s);
 
+// pairs.cu: scratch of the PP queue's group order for up to n groups.
+size_t order_temp_bytes(int64_t n);
+
 // sort.cu: stable LSD radix sort of (key, value) pairs on the low `bits` bits.
 size_t sort_temp_bytes(int64_t n);
 int radix_sort_pairs(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int32_t *vals_alt, int64_t n, int bits,

@@ -1,7 +1,8 @@
 // PP direct summation over the cutoff leaf-pair list.
 //
 // One warp takes one target group at a time from a global queue (the task
-// queue of Sec. 4.3, ground cells rolled in ascending order) and holds one
+// queue of Sec. 4.3; in the pair builder's order of decreasing cost, or in
+// ground-cell order along the curve) and holds one
 // target particle per lane in registers.  The source leaves of the group's
 // list are streamed through shared memory: lanes load the leaves' particles
 // with float4 loads (32 useful loads per round whatever the leaf sizes),
@@ -83,6 +84,7 @@ struct PPArgs {
     const float2 *table;
     float tab_scale2;                // (kTabN / rcut)^2
     int64_t n_pos;                   // rows of pos_leaf (bounds checks)
+    const int32_t *order;            // queue slot -> group (groups by decreasing cost), or NULL
 };
 
 struct Kahan3 {
@@ -467,7 +469,10 @@ __global__ void __launch_bounds__(kPPThreads, kMinBlocks) k_pp(PPArgs a)
     }
     for (;;) {
         int g = 0;
-        if (lane == 0) g = atomicAdd(a.queue, 1);
+        if (lane == 0) {
+            g = atomicAdd(a.queue, 1);
+            if (a.order && g < ng) g = a.order[g];   // the queue's order (a permutation of the groups)
+        }
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
         const int i0 = a.group_first[g], ni = a.group_first[g + 1] - i0;
@@ -895,6 +900,7 @@ static void pp_args(const ph_leaves *lv, const ph_pairs *pr, float *d_acc, PPArg
     a.entries = pr ? static_cast<const float4 *>(pr->entries.p) : nullptr;
     a.ecount = pr ? static_cast<const uint8_t *>(pr->ecount.p) : nullptr;
     a.cap = pr ? pr->capacity : 0;
+    a.order = pr && pr->ordered ? static_cast<const int32_t *>(pr->group_order.p) : nullptr;
     a.group_cell = static_cast<const int32_t *>(lv->group_cell.p);
     a.group_c4 = static_cast<const float4 *>(lv->group_c4.p);
     a.group_r4 = static_cast<const float4 *>(lv->group_r4.p);

@@ -188,6 +188,61 @@ def test_kernel_variants_give_identical_forces(gpu_lib):
         B.ph_free(h)
 
 
+def _expected_queue(view):
+    """The documented queue order, restated on the host from the list: a
+    group's cost is the source particles of its entries (a leaf entry holds
+    count + 1 particles, a mass-centre entry one); the key is 255 minus its
+    quarter-octave class (0 for cost 0, else 1 + 4 e + f with 2^e <= cost <
+    2^(e+1) and f the two bits below the leading one); groups in increasing
+    key, ties in group order."""
+    off = view["group_off"].cpu().numpy()
+    per_entry = view["counts"].cpu().numpy().astype(np.int64) + 1
+    csum = np.concatenate([[0], np.cumsum(per_entry)])
+    cost = csum[off[1:]] - csum[off[:-1]]
+    key = np.full(cost.size, 255, np.int64)
+    for g, c in enumerate(cost.tolist()):
+        if c > 0:
+            e = int(c).bit_length() - 1
+            f = (c >> (e - 2)) & 3 if e >= 2 else (c << (2 - e)) & 3
+            key[g] = 255 - (1 + 4 * e + f)
+    return np.argsort(key, kind="stable").astype(np.int32), cost
+
+
+@pytest.mark.parametrize("case", ["batch", "nfw_tree"])
+def test_queue_takes_groups_by_decreasing_cost(gpu_lib, case):
+    import torch
+    B = gpu_lib
+    if case == "batch":
+        ps = synth.batch_boxes(12, seed=7, n_min=300, n_max=6000)
+        theta = 0.0
+    else:
+        ps = synth.workload("nfw_mix_256", scale=24)
+        theta = 0.3
+    pos, mass, acc = _tensors(ps)
+    outs = []
+    for order in (0, 1):
+        prm = [B.make_params(bp.L, bp.G, bp.eps, bp.rs, bp.rcut, 32, B.PH_KEY_HILBERT, theta=theta,
+                             queue_order=order) for bp in ps.boxes]
+        lv = B.ph_build_leaves_batched(pos, mass, ps.offsets, prm)
+        pr = B.ph_leaf_pairs(lv)
+        B.ph_pp_accel(lv, pr, B.PH_G_EXACT, None, acc)
+        torch.cuda.synchronize()
+        outs.append(acc.cpu().numpy().copy())
+        v = B.ph_pairs_get_view(pr)
+        if order == 0:
+            want, cost = _expected_queue(v)
+            got = v["group_order"].cpu().numpy()
+            np.testing.assert_array_equal(got, want)
+            assert np.all(np.diff(cost[got]) <= cost[got][:-1] * 0.25 + 1e-9)   # non-increasing up to a class
+            assert not np.array_equal(got, np.arange(got.size))                 # the case is reordered
+        else:
+            assert v["group_order"] is None
+        for h in (pr, lv):
+            B.ph_free(h)
+    # the order changes which warp takes a group, not the sums
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_autotuner_picks_a_tried_candidate(gpu_lib, tmp_path):
     import torch
     B = gpu_lib
