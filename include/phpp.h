@@ -102,11 +102,13 @@ extern "C" {
  *   queue_order order in which the PP kernel's warps take the target groups
  *             (the task queue of Sec. 4.3): 0 (default) = by decreasing
  *             cost, the source particles of the group's list (Sec. 4.4
- *             weighs work by counts), in quarter-octave classes, ties in
- *             group order -- the heaviest groups start first, so the
- *             launch ends on short ones; 1 = plain group order (along the
- *             curve).  Same results (each group is summed by one warp on
- *             its own).  Direct mode (no stored list) takes group order.
+ *             weighs work by counts), in quarter-octave classes (within a
+ *             class in the order the pair builder meets the groups) -- the
+ *             heaviest groups start first, so the launch ends on short
+ *             ones; 1 = plain group order (along the curve).  Same results
+ *             (each group is summed by one warp on its own).  The direct
+ *             mode (no stored list) and the active-particle mode take group
+ *             order.
  *   theta     opening criterion of the tree part (Sec. 3.3), in [0, 1):
  *             0 (default) = every leaf pair by PP (the exact short-range
  *             sum); theta > 0 = a leaf for which both opening angles

@@ -298,11 +298,6 @@ static void free_pairs(ph_pairs *h)
     DevBuf *bufs[] = {&h->group_cnt, &h->group_off, &h->entries, &h->ecount, &h->work, &h->status, &h->temp,
                       &h->acc_tmp, &h->group_key, &h->group_order, &h->order_temp};
     for (DevBuf *b : bufs) release(*b);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->side) cudaStreamDestroy(h->side);
-    h->ev_fork = h->ev_join = nullptr;
-    h->side = nullptr;
 }
 
 // Set up boxes and buffers for n particles, copy host inputs, launch the build.
@@ -560,23 +555,6 @@ int ph_leaf_pairs(ph_leaves *leaves, void *stream, ph_pairs **pairs)
         rc = ensure(p->group_key, N);
         if (!rc) rc = ensure(p->group_order, 4 * N);
         if (!rc) rc = ensure(p->order_temp, order_temp_bytes((int64_t)N));
-        if (!rc && !p->side) {
-            // the order's stream and its fork / join events (made here, never
-            // inside a capture); without them the order runs on `stream`
-            cudaStream_t side = nullptr;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess &&
-                cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess) {
-                p->side = side;
-                p->ev_fork = e0;
-                p->ev_join = e1;
-            } else {
-                if (e0) cudaEventDestroy(e0);
-                if (side) cudaStreamDestroy(side);
-                cudaGetLastError();
-            }
-        }
     }
     if (!rc && !p->status.p) {
         rc = ensure(p->status, 16);

@@ -97,10 +97,6 @@ struct ph_pairs {
     phpp::DevBuf group_order;    // int32[n]: groups in queue order
     phpp::DevBuf order_temp;     // histograms and scan scratch
     bool ordered = false;
-    // the order is made on a second stream while the fill pass runs (joined
-    // back before the list is complete); null: on the caller's stream
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace phpp {

@@ -14,12 +14,16 @@
 //
 // The count pass also gives each group its cost, the source particles its
 // list holds (a warp's time on a group is proportional to them: it runs all
-// 32 lanes whatever the group's size), and the groups are then ordered by
+// 32 lanes whatever the group's size), and the groups are ordered by
 // decreasing cost for the PP kernel's queue (Sec. 4.4 weighs work by
 // particle counts): the heaviest groups start first, so that the last ones
-// to finish are short.  The order is a stable counting sort on the cost's
-// quarter-octave (8-bit key), so it is deterministic, and the forces do not
-// depend on it (each group is summed by one warp on its own).  The stored
+// to finish are short.  The order is a counting sort on the cost's
+// quarter-octave class (an 8-bit key) folded into the two passes: the count
+// pass counts the groups of each key, and the fill pass, which has the
+// counts, places each group after the keys below its own with an atomic
+// cursor per key.  Groups of one key land in the order the fill pass meets
+// them; the forces do not depend on the order (each group is summed by one
+// warp on its own).  The stored
 // offset of an accepted pair is the difference of the reference points
 // rounded once to FP32: in FP32 directly when no periodic image is involved
 // (the reference points are FP32 numbers), from the FP64 points otherwise.
@@ -42,6 +46,8 @@ struct PairArgs {
     const float4 *leaf_r4, *group_r4;   // the reference points as (exact) FP32
     int64_t *cnt;            // count pass output [n_groups]
     uint8_t *gkey;           // count pass output [n_groups]: queue key (255 - cost bucket), or NULL
+    int32_t *ohist;          // [256] groups per key (count pass), then [256] cursors (fill pass)
+    int32_t *order;          // fill pass output [n_groups]: the queue's order
     const int64_t *off;      // fill pass input   [n_groups + 1]
     float4 *ent;             // fill pass output: offset x, y, z, first source particle (bits)
     uint8_t *ecnt;           // fill pass output: particles in the leaf - 1
@@ -72,6 +78,8 @@ __device__ __forceinline__ int warp_incl_scan_i(int v, int lane)
 // the number of runs started before q0 plus the start bits at or below t,
 // minus one (lanes with no leaves start no run).  Candidates keep the order
 // (neighbour, leaf), so the list is deterministic.
+constexpr int kOrdKeys = 256;   // queue keys (8 bits)
+
 // Quarter-octave bucket of a cost: 0 for 0, else 1 + 4 e + f with e the
 // position of the leading bit and f the next two bits (1 .. 128).
 __device__ __forceinline__ int cost_bucket(unsigned c)
@@ -91,8 +99,27 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
     const unsigned lt = (1u << lane) - 1u;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int ng = *a.n_groups;
+    __shared__ int32_t s_start[kOrdKeys];   // fill pass with an order: first slot of each key
+    if (kFill && a.order) {
+        // exclusive scan of the per-key counts (one thread per key)
+        static_assert(kThreads == kOrdKeys, "one thread per key");
+        const int c = a.ohist[threadIdx.x];
+        int incl = warp_incl_scan_i(c, lane);
+        __shared__ int32_t s_wsum[kThreads / 32];
+        if (lane == 31) s_wsum[w] = incl;
+        __syncthreads();
+        for (int ww = 0; ww < w; ww++) incl += s_wsum[ww];
+        s_start[threadIdx.x] = incl - c;
+        __syncthreads();
+    }
     for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ng; gi += warps) {
         const int g = a.group_list ? a.group_list[gi] : gi;
+        if (kFill && a.order && lane == 0) {
+            // this group's place in the queue: after every group of a lower key
+            const int k = a.gkey[g];
+            const int pos = s_start[k] + atomicAdd(&a.ohist[kOrdKeys + k], 1);
+            if (in_bounds(pos, ng, BS_ORDER)) a.order[pos] = g;
+        }
         const BoxDev &bx = a.boxes[a.group_box[g]];
         const int ns = bx.nside;
         const int ground = a.group_cell[g] - bx.cell_base;
@@ -220,115 +247,21 @@ __global__ void __launch_bounds__(kThreads) k_pairs(PairArgs a)
             const unsigned cost = __reduce_add_sync(0xffffffffu, src);
             if (lane == 0) {
                 a.cnt[g] = count;
-                if (a.gkey) a.gkey[g] = (uint8_t)(255 - cost_bucket(cost));
+                if (a.gkey) {
+                    const int k = 255 - cost_bucket(cost);
+                    a.gkey[g] = (uint8_t)k;
+                    atomicAdd(&a.ohist[k], 1);
+                }
             }
         }
         __syncwarp();   // s_run is rewritten for the next group
     }
 }
 
-// Stable counting sort of the groups by their 8-bit queue key.  The groups
-// are cut into kOrdChunks equal chunks (sized from the device-side group
-// count, so the launches do not depend on it): per-chunk histograms
-// (key-major), one exclusive scan over them, then each chunk ranks its keys
-// in order -- 2048 at a time, warp by warp, 32 per round -- and writes each
-// group's index after the same keys of earlier chunks and earlier rounds.
-constexpr int kOrdItems = 8;
-constexpr int kOrdWarps = kThreads / 32;
-constexpr int kOrdSub = kThreads * kOrdItems;   // groups ranked per pass of a chunk
-constexpr int kOrdBins = 256;
-constexpr int kOrdChunks = 128;
-static_assert(kThreads == kOrdBins, "one thread per key value");
-
-__device__ __forceinline__ void order_chunk(int ng, int &c0, int &c1)
-{
-    const int chunk = (ng + kOrdChunks - 1) / kOrdChunks;
-    c0 = min(ng, (int)blockIdx.x * chunk);
-    c1 = min(ng, c0 + chunk);
-}
-
-__global__ void __launch_bounds__(kThreads) k_order_hist(const uint8_t *key, const int32_t *n_groups, int32_t *hist)
-{
-    __shared__ int32_t h[kOrdBins];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    int c0, c1;
-    order_chunk(*n_groups, c0, c1);
-    for (int i = c0 + threadIdx.x; i < c1; i += kThreads) atomicAdd(&h[key[i]], 1);
-    __syncthreads();
-    hist[threadIdx.x * kOrdChunks + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(kThreads) k_order_scatter(const uint8_t *key, const int32_t *n_groups,
-                                                             const int32_t *offsets, int32_t *order)
-{
-    __shared__ int32_t cnt[kOrdWarps][kOrdBins];
-    __shared__ int32_t next[kOrdBins];   // next slot of each key for this chunk
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int ng = *n_groups;
-    int c0, c1;
-    order_chunk(ng, c0, c1);
-    next[threadIdx.x] = offsets[threadIdx.x * kOrdChunks + blockIdx.x];
-    for (int sub = c0; sub < c1; sub += kOrdSub) {
-        for (int d = lane; d < kOrdBins; d += 32) cnt[w][d] = 0;
-        __syncwarp();
-        // warp w ranks groups [base, base + 256) of this pass, 32 per round, in order
-        const int base = sub + w * 32 * kOrdItems;
-        int d_[kOrdItems], r_[kOrdItems];
-#pragma unroll
-        for (int r = 0; r < kOrdItems; r++) {
-            const int i = base + r * 32 + lane;
-            const bool ok = i < c1;
-            const int d = ok ? (int)key[i] : kOrdBins;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            int old = 0;
-            if (ok && lane == leader) old = cnt[w][d];
-            old = __shfl_sync(0xffffffffu, old, leader);
-            __syncwarp();
-            if (ok && lane == leader) cnt[w][d] = old + __popc(peers);
-            __syncwarp();
-            d_[r] = d;
-            r_[r] = old + __popc(peers & lt);
-        }
-        __syncthreads();
-        int total;
-        {   // per key value: exclusive prefix of the per-warp counts over warps
-            const int d = threadIdx.x;
-            int run = 0;
-#pragma unroll
-            for (int ww = 0; ww < kOrdWarps; ww++) {
-                const int c = cnt[ww][d];
-                cnt[ww][d] = run;
-                run += c;
-            }
-            total = run;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kOrdItems; r++) {
-            if (d_[r] < kOrdBins) {
-                const int pos = next[d_[r]] + cnt[w][d_[r]] + r_[r];
-                if (in_bounds(pos, ng, BS_ORDER)) order[pos] = base + r * 32 + lane;
-            }
-        }
-        __syncthreads();
-        next[threadIdx.x] += total;
-        __syncthreads();
-    }
-}
-
 }  // namespace
 
-// Scratch of the group order: the per-chunk histograms and their scan, and
-// the scan's own scratch (the same for any number of groups).
-size_t order_temp_bytes(int64_t)
-{
-    size_t counts = (size_t)(kOrdBins * kOrdChunks + 1) * sizeof(int32_t);   // the scan also writes out[n]
-    counts = (counts + 255) & ~(size_t)255;
-    return 2 * counts + scan_temp_bytes(kOrdBins * kOrdChunks);
-}
+// Scratch of the group order: the per-key counts and cursors.
+size_t order_temp_bytes(int64_t) { return 2 * kOrdKeys * sizeof(int32_t); }
 
 // The sizing (with `sizing_sync`: read the total, grow the entry buffers)
 // and the fill pass, on stream s.
@@ -392,9 +325,14 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     }
     a.n_particles = lv->n;
     a.cnt = static_cast<int64_t *>(pr->group_cnt.p);
-    // the cost order (queue_order 0) where the handle has its buffers
-    const bool ordered = lv->queue_order == 0 && pr->group_key.p && pr->group_order.p && pr->order_temp.p;
+    // the cost order (queue_order 0) where the handle has its buffers; not in
+    // the active-particle mode, whose inactive groups get no list (the PP
+    // kernel takes them in group order there)
+    const bool ordered =
+        lv->queue_order == 0 && !lv->active && pr->group_key.p && pr->group_order.p && pr->order_temp.p;
     a.gkey = ordered ? static_cast<uint8_t *>(pr->group_key.p) : nullptr;
+    a.ohist = ordered ? static_cast<int32_t *>(pr->order_temp.p) : nullptr;
+    a.order = ordered ? static_cast<int32_t *>(pr->group_order.p) : nullptr;
     pr->ordered = ordered;
     a.off = static_cast<const int64_t *>(pr->group_off.p);
     a.status = static_cast<uint32_t *>(pr->status.p);
@@ -402,49 +340,18 @@ int build_pairs_device(const ph_leaves *lv, ph_pairs *pr, cudaStream_t s, bool s
     const int grid = 152 * 8;
     const int32_t *n_all = static_cast<const int32_t *>(lv->counts.p) + 1;
     if (lv->active) {
-        int rz = cuda_check(cudaMemsetAsync(a.cnt, 0, 8 * (size_t)(n > 0 ? n : 1), s), "clear counts");
-        if (!rz && a.gkey) rz = cuda_check(cudaMemsetAsync(a.gkey, 0xFF, (size_t)(n > 0 ? n : 1), s), "clear keys");
+        const int rz = cuda_check(cudaMemsetAsync(a.cnt, 0, 8 * (size_t)(n > 0 ? n : 1), s), "clear counts");
+        if (rz) return rz;
+    }
+    if (ordered) {
+        const int rz = cuda_check(cudaMemsetAsync(a.ohist, 0, order_temp_bytes(0), s), "clear key counts");
         if (rz) return rz;
     }
     k_pairs<false><<<grid, kThreads, 0, s>>>(a);
     count_launch();
     int rc = scan_exclusive_i64(a.cnt, static_cast<int64_t *>(pr->group_off.p), n, n_all, pr->temp.p, s);
     if (rc) return rc;
-    // the PP queue's order: all groups (the inactive ones of the
-    // active-particle mode last, with cost 0), on the side stream while the
-    // sizing and the fill pass run on `s`; every path after the fork joins
-    // it back, so a capture never ends with the side stream forked
-    cudaStream_t os = s;
-    if (ordered && pr->side && pr->ev_fork && pr->ev_join) {
-        rc = cuda_check(cudaEventRecord(pr->ev_fork, s), "order fork");
-        if (!rc) rc = cuda_check(cudaStreamWaitEvent(pr->side, pr->ev_fork, 0), "order fork wait");
-        if (rc) return rc;
-        os = pr->side;
-    }
-    if (ordered) {
-        size_t counts = (size_t)(kOrdBins * kOrdChunks + 1) * sizeof(int32_t);
-        counts = (counts + 255) & ~(size_t)255;
-        int32_t *hist = static_cast<int32_t *>(pr->order_temp.p);
-        int32_t *offs = reinterpret_cast<int32_t *>(static_cast<char *>(pr->order_temp.p) + counts);
-        void *scan_tmp = static_cast<char *>(pr->order_temp.p) + 2 * counts;
-        k_order_hist<<<kOrdChunks, kThreads, 0, os>>>(a.gkey, n_all, hist);
-        count_launch();
-        rc = scan_exclusive_i32(hist, offs, (int64_t)kOrdBins * kOrdChunks, nullptr, scan_tmp, os);
-        if (!rc) {
-            k_order_scatter<<<kOrdChunks, kThreads, 0, os>>>(a.gkey, n_all, offs,
-                                                             static_cast<int32_t *>(pr->group_order.p));
-            count_launch();
-        }
-    }
-    if (!rc) rc = fill_pairs(pr, a, n_all, grid, s, sizing_sync);
-    if (os != s) {
-        const int rj = cuda_check(cudaEventRecord(pr->ev_join, os), "order join");
-        if (!rc) rc = rj;
-        if (!rj) {
-            const int rw = cuda_check(cudaStreamWaitEvent(s, pr->ev_join, 0), "order join wait");
-            if (!rc) rc = rw;
-        }
-    }
+    rc = fill_pairs(pr, a, n_all, grid, s, sizing_sync);
     if (rc) return rc;
     return cuda_check(cudaGetLastError(), "pair kernels");
 }

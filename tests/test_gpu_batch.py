@@ -188,13 +188,12 @@ def test_kernel_variants_give_identical_forces(gpu_lib):
         B.ph_free(h)
 
 
-def _expected_queue(view):
-    """The documented queue order, restated on the host from the list: a
-    group's cost is the source particles of its entries (a leaf entry holds
-    count + 1 particles, a mass-centre entry one); the key is 255 minus its
-    quarter-octave class (0 for cost 0, else 1 + 4 e + f with 2^e <= cost <
-    2^(e+1) and f the two bits below the leading one); groups in increasing
-    key, ties in group order."""
+def _queue_keys(view):
+    """The documented queue key of every group, restated on the host from
+    the list: a group's cost is the source particles of its entries (a leaf
+    entry holds count + 1 particles, a mass-centre entry one); the key is 255
+    minus its quarter-octave class (0 for cost 0, else 1 + 4 e + f with
+    2^e <= cost < 2^(e+1) and f the two bits below the leading one)."""
     off = view["group_off"].cpu().numpy()
     per_entry = view["counts"].cpu().numpy().astype(np.int64) + 1
     csum = np.concatenate([[0], np.cumsum(per_entry)])
@@ -205,7 +204,7 @@ def _expected_queue(view):
             e = int(c).bit_length() - 1
             f = (c >> (e - 2)) & 3 if e >= 2 else (c << (2 - e)) & 3
             key[g] = 255 - (1 + 4 * e + f)
-    return np.argsort(key, kind="stable").astype(np.int32), cost
+    return key, cost
 
 
 @pytest.mark.parametrize("case", ["batch", "nfw_tree"])
@@ -230,10 +229,12 @@ def test_queue_takes_groups_by_decreasing_cost(gpu_lib, case):
         outs.append(acc.cpu().numpy().copy())
         v = B.ph_pairs_get_view(pr)
         if order == 0:
-            want, cost = _expected_queue(v)
+            key, cost = _queue_keys(v)
             got = v["group_order"].cpu().numpy()
-            np.testing.assert_array_equal(got, want)
-            assert np.all(np.diff(cost[got]) <= cost[got][:-1] * 0.25 + 1e-9)   # non-increasing up to a class
+            # a permutation of the groups in non-decreasing key (decreasing cost class)
+            np.testing.assert_array_equal(np.sort(got), np.arange(key.size))
+            assert np.all(np.diff(key[got]) >= 0)
+            assert np.all(np.diff(cost[got]) <= cost[got][:-1] * 0.25 + 1e-9)   # within a class: < 25 %
             assert not np.array_equal(got, np.arange(got.size))                 # the case is reordered
         else:
             assert v["group_order"] is None
