@@ -27,7 +27,8 @@ particles and ghosts with the others over NCCL (the packing in the
 library's kernels) and computes its own particles' forces; value is the
 whole box's interactions per second of the slowest rank (strong scaling).
 --replicas runs N independent whole-box replicas instead (weak scaling);
---partitioned runs the domain path with one rank too.
+--partitioned runs the domain path with one rank too.  --jsonl PATH also
+appends the result line to PATH, one line per run.
 """
 from __future__ import annotations
 
@@ -595,7 +596,7 @@ def run_reference(args, rank):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -863,7 +864,7 @@ def run_ours(args, rank, world, local_rank):
     for h in (graph, pr, lv, pr2, lv2):
         B.ph_free(h)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line, args)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -968,8 +969,20 @@ def run_partitioned(args, rank, world, local_rank):
             "gpu_launches": launches, "clocks": clk,
             "partition": {"own_particles": own_total, "largest_local_set": local_max},
         }
-        print(json.dumps(line), flush=True)
+        emit(line, args)
     dist.destroy_process_group()
+
+
+def emit(line, args):
+    """The run's one JSON line: on stdout, and appended to the --jsonl file
+    (one line per run, so successive runs form a JSONL log)."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    path = getattr(args, "jsonl", None)
+    if path:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "a") as f:
+            f.write(text + "\n")
 
 
 def main():
@@ -993,6 +1006,7 @@ def main():
                          "is the default)")
     ap.add_argument("--replicas", action="store_true",
                     help="with several ranks: independent whole-box replicas instead of the domain decomposition")
+    ap.add_argument("--jsonl", default="", help="also append the result line to this file (a JSONL run log)")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

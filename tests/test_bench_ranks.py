@@ -60,3 +60,15 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
         line = json.loads(lines[-1])
         assert line["impl"] == "reference" and line["unit"] == "interactions/s" and line["value"] > 0
         assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_result_lines_append_to_a_jsonl_log(tmp_path):
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    path = tmp_path / "runs" / "bench.jsonl"
+    for k in range(2):
+        bench.emit({"metric": "m", "value": float(k)}, argparse.Namespace(jsonl=str(path)))
+    rows = [json.loads(x) for x in path.read_text().splitlines()]
+    assert rows == [{"metric": "m", "value": 0.0}, {"metric": "m", "value": 1.0}]
+    bench.emit({"metric": "m"}, argparse.Namespace(jsonl=""))   # no log: stdout only
