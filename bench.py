@@ -69,8 +69,8 @@ PAPER_FLOPS_PER_INTERACTION = 22   # the convention of Sec. 5
 # Peano-Hilbert keys.  None for any other configuration, or once the kernel
 # has changed since the capture.
 PP_TRAFFIC = {   # (workload, scale, leaf_max, levels, variant, group, key) -> bytes
-    ("zeldovich_128", 0, 32, 1, 0, 32, 1): 194206720 + 18382080,
-    ("zeldovich_128", 0, 16, 1, 0, 32, 1): 263585280 + 19879680,
+    ("zeldovich_128", 0, 32, 1, 0, 32, 1): 239986432 + 24170496,
+    ("zeldovich_128", 0, 16, 1, 0, 32, 1): 345537536 + 29011968,
 }
 
 
