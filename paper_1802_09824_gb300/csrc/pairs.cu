@@ -10,7 +10,10 @@
 // images; at most one of them can be within R_cut < L/2 of any particle).
 //
 // The test runs in FP32 on cell-relative centres with a relative margin on
-// R_cut, so no pair the PP kernel could accept is ever dropped.
+// R_cut, so no pair the PP kernel could accept is ever dropped.  The stored
+// offset of an accepted pair is the difference of the reference points
+// rounded once to FP32: in FP32 directly when no periodic image is involved
+// (the reference points are FP32 numbers), from the FP64 points otherwise.
 //
 // The count pass also gives each group its cost, the source particles its
 // list holds (a warp's time on a group is proportional to them: it runs all
@@ -23,10 +26,7 @@
 // counts, places each group after the keys below its own with an atomic
 // cursor per key.  Groups of one key land in the order the fill pass meets
 // them; the forces do not depend on the order (each group is summed by one
-// warp on its own).  The stored
-// offset of an accepted pair is the difference of the reference points
-// rounded once to FP32: in FP32 directly when no periodic image is involved
-// (the reference points are FP32 numbers), from the FP64 points otherwise.
+// warp on its own).
 #include "checks.cuh"
 #include "handles.cuh"
 
