@@ -182,7 +182,9 @@ int ph_build_leaves_batched(const void *pos, int pos_type, const float *mass,
  * within rcut of the group's bounding box (Sec. 3.3: leaf-leaf interactions
  * go to the PP kernel).  Stored per entry: the FP32 offset (leaf reference -
  * group reference, computed in FP64, image included), the leaf's first
- * particle and its particle count.
+ * particle and its particle count.  With queue_order 0 the same passes
+ * also order the groups by decreasing cost for the PP kernel's queue (see
+ * ph_params).
  * Synchronises the stream once to size the list, unless the handle was given
  * a fixed capacity with ph_pairs_reserve (then overflow is latched as
  * PH_ERR_CAPACITY and no entry beyond the capacity is written).
